@@ -1,0 +1,364 @@
+/*
+ * fsgp_oracle.c -- plain CPU oracle for synchronous batched Monte Carlo propagation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct restatement of
+ * what the GPU library computes.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it.  It shares no code, header, table
+ * or helper with the CUDA library: it has its own Philox4x32-10, its own survival
+ * table and its own update rules, each written from the paper's definitions.
+ *
+ * Shape (paper, Algorithm 1): for each realization, for each step, for each node,
+ * read the step-(k-1) states of the node and its in-neighbours and write the step-k
+ * state into a second buffer (the X^{k+1} <- X^k double buffer of Algorithm 1;
+ * node-synchronous update, Eq. (all), Eqs. (ms), (agg), (updata) of Sec. 3.1).
+ * Realizations are independent (batched Monte Carlo definition, Eq. (batch)), so the
+ * only parallelism here is threads over realizations.
+ *
+ * Integer readings of the paper (all listed in the design notes):
+ *  - SIR (Appendix A.1, micro-accelerated SIR): a susceptible node with k infected
+ *    in-neighbours is infected with probability 1-(1-beta)^k.  Here the probability
+ *    is the exact integer survival table surv[0]=2^32, surv[k]=floor(surv[k-1]*q/2^32),
+ *    q=2^32-llrint(beta*2^32), and the node is infected iff its 32-bit uniform
+ *    u >= surv[k] (the survival form of "U < m_i").  An infected node recovers iff
+ *    u_rec < llrint(gamma*2^32) (delta of the appendix read as gamma).
+ *  - SIS: the same with I -> S instead of I -> R (Table 1 model, rules not written
+ *    out in the paper).
+ *  - IC (Kempe et al., cited in Sec. 2): each in-arc (w -> v) is tried once, at the
+ *    step after w activates, if v is still inactive; live iff u*d_in(v) < 2^32
+ *    (weighted cascade) or u < llrint(p*2^32) (constant p).
+ *  - LT (named in Sec. 1; definition taken from the project statement): per node and
+ *    realization threshold theta = u(tag 4, v, t=0, r); an inactive node with k >= 1
+ *    active in-arcs activates iff k*2^32 >= theta*d_in(v).
+ *
+ * Uniforms (bit-plane contract): P_j = Philox4x32_10(key=(lo32(seed),hi32(seed)),
+ * ctr=(a, t, r>>5, (tag<<8)|(j>>2)))[j&3] for j = 0..31, and bit (31-j) of u is bit
+ * (r&31) of P_j.  This oracle always assembles all 32 bits.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+#include <pthread.h>
+
+#define ORC_SIR 0
+#define ORC_SIS 1
+#define ORC_IC 2
+#define ORC_LT 3
+
+#define TAG_INFECT 1u
+#define TAG_RECOVER 2u
+#define TAG_IC_EDGE 3u
+#define TAG_LT_THRESH 4u
+
+/* node states.  SIR/SIS: 0=S 1=I 2=R.  IC/LT: 0=inactive 1=newly active (frontier)
+ * 2=active since an earlier step. */
+#define ST_0 0
+#define ST_1 1
+#define ST_2 2
+
+/* ---------------- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) --------------
+ * One round: two 32x32->64 multiplies of counter words 0 and 2 by the round
+ * multipliers; the high halves are xored with the other counter words and the key,
+ * the low halves pass through.  The key is bumped by the Weyl constants (golden ratio
+ * and sqrt(3)-1 scaled to 2^32) between rounds.  Ten rounds. */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* The 32-bit uniform of realization r for (tag, subject a, step t). */
+uint32_t orc_uniform(uint64_t rng_seed, uint32_t tag, uint32_t a, uint32_t t, uint32_t r)
+{
+    uint32_t key[2] = {(uint32_t)(rng_seed & 0xFFFFFFFFu), (uint32_t)(rng_seed >> 32)};
+    uint32_t u = 0;
+    for (uint32_t call = 0; call < 8; ++call) {
+        uint32_t ctr[4] = {a, t, r >> 5, (tag << 8) | call};
+        uint32_t out[4];
+        orc_philox4x32_10(ctr, key, out);
+        for (uint32_t i = 0; i < 4; ++i) {
+            uint32_t j = call * 4 + i;               /* plane index, MSB first */
+            uint32_t bit = (out[i] >> (r & 31u)) & 1u;
+            u |= bit << (31u - j);
+        }
+    }
+    return u;
+}
+
+/* Exact integer survival table: surv[k] ~ 2^32 (1-beta)^k, for k = 0..kmax. */
+void orc_survival_table(double beta, int64_t kmax, uint64_t *surv)
+{
+    uint64_t b = (uint64_t)llrint(beta * 4294967296.0);
+    uint64_t q = 4294967296ull - b;
+    surv[0] = 4294967296ull;
+    for (int64_t k = 1; k <= kmax; ++k) {
+        /* q = 2^32 (beta rounds to 0) would overflow the 64-bit product: then the
+         * survival probability is exactly 1 at every k. */
+        if (q == 4294967296ull) surv[k] = surv[k - 1];
+        else surv[k] = (surv[k - 1] * q) >> 32;
+    }
+}
+
+uint64_t orc_prob_threshold(double p)
+{
+    return (uint64_t)llrint(p * 4294967296.0);
+}
+
+/* ---------------- one simulation ---------------- */
+
+typedef struct {
+    int model;
+    int32_t n;
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+    double beta, gamma;
+    int ic_mode;          /* 0 = weighted cascade (1/d_in), 1 = constant probability */
+    double ic_p;
+    const int32_t *seeds;
+    int64_t n_seeds;
+    int32_t T;
+    uint64_t rng_seed;
+    const uint8_t *init_state; /* optional [n_real][n] start states (resume); NULL = seeds */
+    int32_t t0;               /* absolute index of the starting step */
+    int32_t r_lo, n_real;     /* realizations r_lo .. r_lo+n_real-1 */
+    /* outputs */
+    uint64_t *counts;     /* [T+1][3], summed over the realizations run */
+    uint32_t *per_real;   /* optional [n_real][T+1][3] */
+    uint32_t *freq;       /* optional [3][n] */
+    uint8_t *final_state; /* optional [n_real][n] */
+    int32_t *quiet_step;  /* [n_real]: IC/LT first step with an empty frontier (T if never) */
+    /* derived */
+    uint64_t *surv;
+    int64_t kmax;
+    uint64_t g_rec;
+    uint64_t p_const;
+} orc_job;
+
+typedef struct {
+    orc_job *job;
+    int tid, nthreads;
+    uint64_t *counts;  /* thread-local [T+1][3] */
+    uint32_t *freq;    /* thread-local [3][n] or NULL */
+} orc_worker;
+
+/* One synchronous step of node v for realization r: returns the state of v at step t
+ * given the states X of step t-1 (Eq. nodestate of Sec. 2). */
+static uint8_t node_update(const orc_job *jb, const uint8_t *X, int32_t v, uint32_t t, uint32_t r)
+{
+    const int32_t beg = jb->row_ptr[v], end = jb->row_ptr[v + 1];
+    const int64_t d = (int64_t)end - beg;
+    const uint8_t s = X[v];
+    switch (jb->model) {
+    case ORC_SIR:
+    case ORC_SIS: {
+        if (s == ST_0) {
+            int64_t k = 0;
+            for (int32_t e = beg; e < end; ++e)
+                if (X[jb->col_idx[e]] == ST_1) ++k;
+            if (k == 0) return ST_0;
+            uint32_t u = orc_uniform(jb->rng_seed, TAG_INFECT, (uint32_t)v, t, r);
+            uint64_t thr = jb->surv[k <= jb->kmax ? k : jb->kmax];
+            return ((uint64_t)u >= thr) ? ST_1 : ST_0;
+        }
+        if (s == ST_1) {
+            uint32_t u = orc_uniform(jb->rng_seed, TAG_RECOVER, (uint32_t)v, t, r);
+            if ((uint64_t)u < jb->g_rec) return jb->model == ORC_SIR ? ST_2 : ST_0;
+            return ST_1;
+        }
+        return ST_2;
+    }
+    case ORC_IC: {
+        if (s != ST_0) return ST_2;
+        for (int32_t e = beg; e < end; ++e) {
+            if (X[jb->col_idx[e]] != ST_1) continue;
+            uint32_t u = orc_uniform(jb->rng_seed, TAG_IC_EDGE, (uint32_t)e, t, r);
+            int live;
+            if (jb->ic_mode == 0) live = ((uint64_t)u * (uint64_t)d) < 4294967296ull;
+            else live = (uint64_t)u < jb->p_const;
+            if (live) return ST_1;
+        }
+        return ST_0;
+    }
+    case ORC_LT: {
+        if (s != ST_0) return ST_2;
+        int64_t k = 0;
+        for (int32_t e = beg; e < end; ++e)
+            if (X[jb->col_idx[e]] != ST_0) ++k;
+        if (k == 0) return ST_0;
+        uint32_t theta = orc_uniform(jb->rng_seed, TAG_LT_THRESH, (uint32_t)v, 0u, r);
+        /* k*2^32 >= theta*d, both sides < 2^63 for k, d < 2^31 */
+        if (((uint64_t)k << 32) >= (uint64_t)theta * (uint64_t)d) return ST_1;
+        return ST_0;
+    }
+    }
+    return s;
+}
+
+static void tally(const orc_job *jb, const uint8_t *X, uint64_t *cnt3)
+{
+    uint64_t c[3] = {0, 0, 0};
+    for (int32_t v = 0; v < jb->n; ++v) c[X[v]]++;
+    cnt3[0] += c[0]; cnt3[1] += c[1]; cnt3[2] += c[2];
+}
+
+static void *worker_main(void *arg)
+{
+    orc_worker *w = (orc_worker *)arg;
+    orc_job *jb = w->job;
+    const int32_t n = jb->n, T = jb->T;
+    uint8_t *X = (uint8_t *)malloc((size_t)n > 0 ? (size_t)n : 1);
+    uint8_t *Y = (uint8_t *)malloc((size_t)n > 0 ? (size_t)n : 1);
+    for (int32_t ri = w->tid; ri < jb->n_real; ri += w->nthreads) {
+        const uint32_t r = (uint32_t)(jb->r_lo + ri);
+        /* X^0 */
+        if (jb->init_state) {
+            memcpy(X, jb->init_state + (size_t)ri * n, (size_t)n);
+        } else {
+            memset(X, ST_0, (size_t)n);
+            for (int64_t i = 0; i < jb->n_seeds; ++i) X[jb->seeds[i]] = ST_1;
+        }
+        uint64_t c0[3] = {0, 0, 0};
+        tally(jb, X, c0);
+        for (int c = 0; c < 3; ++c) {
+            w->counts[c] += c0[c];
+            if (jb->per_real) jb->per_real[((size_t)ri * (T + 1)) * 3 + c] = (uint32_t)c0[c];
+        }
+        int quiet = 0;
+        int32_t quiet_step = T;
+        if (jb->model == ORC_IC || jb->model == ORC_LT) {
+            int any_front = 0;
+            for (int32_t v = 0; v < n; ++v) if (X[v] == ST_1) { any_front = 1; break; }
+            if (!any_front) { quiet = 1; quiet_step = 0; }
+        }
+        for (int32_t k = 1; k <= T; ++k) {
+            if (!quiet) {
+                const uint32_t t = (uint32_t)(jb->t0 + k);
+                for (int32_t v = 0; v < n; ++v) Y[v] = node_update(jb, X, v, t, r);
+                uint8_t *tmp = X; X = Y; Y = tmp;
+                if (jb->model == ORC_IC || jb->model == ORC_LT) {
+                    int any_front = 0;
+                    for (int32_t v = 0; v < n; ++v) if (X[v] == ST_1) { any_front = 1; break; }
+                    if (!any_front) { quiet = 1; quiet_step = k; }
+                }
+            }
+            uint64_t ck[3] = {0, 0, 0};
+            tally(jb, X, ck);
+            for (int c = 0; c < 3; ++c) {
+                w->counts[(size_t)k * 3 + c] += ck[c];
+                if (jb->per_real) jb->per_real[((size_t)ri * (T + 1) + k) * 3 + c] = (uint32_t)ck[c];
+            }
+        }
+        if (jb->quiet_step) jb->quiet_step[ri] = quiet_step;
+        if (w->freq)
+            for (int32_t v = 0; v < n; ++v) w->freq[(size_t)X[v] * n + v]++;
+        if (jb->final_state) memcpy(jb->final_state + (size_t)ri * n, X, (size_t)n);
+    }
+    free(X);
+    free(Y);
+    return NULL;
+}
+
+/*
+ * Run n_real realizations (r_lo .. r_lo+n_real-1) of one model from one seed set.
+ * Returns 0 on success, -1 on invalid arguments, -2 on allocation failure.
+ * counts must hold (T+1)*3 u64, per_real (optional) n_real*(T+1)*3 u32,
+ * freq (optional) 3*n u32, final_state (optional) n_real*n u8, quiet_step
+ * (optional) n_real i32.
+ */
+int orc_simulate(int model, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                 double beta, double gamma, int ic_mode, double ic_p,
+                 const int32_t *seeds, int64_t n_seeds, int32_t T, uint64_t rng_seed,
+                 const uint8_t *init_state, int32_t t0,
+                 int32_t r_lo, int32_t n_real, int nthreads,
+                 uint64_t *counts, uint32_t *per_real, uint32_t *freq, uint8_t *final_state,
+                 int32_t *quiet_step)
+{
+    if (model < 0 || model > 3 || n < 0 || T < 0 || n_real < 0 || r_lo < 0 || !counts) return -1;
+    if (nthreads < 1) nthreads = 1;
+    for (int64_t i = 0; i < n_seeds; ++i)
+        if (seeds[i] < 0 || seeds[i] >= n) return -1;
+    orc_job jb;
+    memset(&jb, 0, sizeof jb);
+    jb.model = model; jb.n = n; jb.row_ptr = row_ptr; jb.col_idx = col_idx;
+    jb.beta = beta; jb.gamma = gamma; jb.ic_mode = ic_mode; jb.ic_p = ic_p;
+    jb.seeds = seeds; jb.n_seeds = n_seeds; jb.T = T; jb.rng_seed = rng_seed;
+    jb.init_state = init_state; jb.t0 = t0;
+    jb.r_lo = r_lo; jb.n_real = n_real;
+    jb.counts = counts; jb.per_real = per_real; jb.freq = freq; jb.final_state = final_state;
+    jb.quiet_step = quiet_step;
+    int64_t maxdeg = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        int64_t d = (int64_t)row_ptr[v + 1] - row_ptr[v];
+        if (d > maxdeg) maxdeg = d;
+    }
+    jb.kmax = maxdeg;
+    jb.surv = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(maxdeg + 1));
+    if (!jb.surv) return -2;
+    orc_survival_table(beta, maxdeg, jb.surv);
+    jb.g_rec = orc_prob_threshold(gamma);
+    jb.p_const = orc_prob_threshold(ic_p);
+
+    memset(counts, 0, sizeof(uint64_t) * (size_t)(T + 1) * 3);
+    if (freq) memset(freq, 0, sizeof(uint32_t) * 3 * (size_t)n);
+    if (nthreads > n_real && n_real > 0) nthreads = n_real;
+    orc_worker *ws = (orc_worker *)calloc((size_t)nthreads, sizeof(orc_worker));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    int rc = 0;
+    for (int i = 0; i < nthreads; ++i) {
+        ws[i].job = &jb; ws[i].tid = i; ws[i].nthreads = nthreads;
+        ws[i].counts = (uint64_t *)calloc((size_t)(T + 1) * 3, sizeof(uint64_t));
+        ws[i].freq = freq ? (uint32_t *)calloc(3 * (size_t)n + 1, sizeof(uint32_t)) : NULL;
+        if (!ws[i].counts || (freq && !ws[i].freq)) rc = -2;
+    }
+    if (rc == 0) {
+        for (int i = 0; i < nthreads; ++i) pthread_create(&th[i], NULL, worker_main, &ws[i]);
+        for (int i = 0; i < nthreads; ++i) pthread_join(th[i], NULL);
+        for (int i = 0; i < nthreads; ++i) {
+            for (size_t j = 0; j < (size_t)(T + 1) * 3; ++j) counts[j] += ws[i].counts[j];
+            if (freq)
+                for (size_t j = 0; j < 3 * (size_t)n; ++j) freq[j] += ws[i].freq[j];
+        }
+    }
+    for (int i = 0; i < nthreads; ++i) { free(ws[i].counts); free(ws[i].freq); }
+    free(ws); free(th); free(jb.surv);
+    return rc;
+}
+
+/* Step-by-step single-node check used for sampled parity at full size: the state of
+ * node v at step t (absolute index) in realization r, from the step-(t-1) states X. */
+int orc_node_step(int model, const int32_t *row_ptr, const int32_t *col_idx, int32_t v,
+                  const uint8_t *X, double beta, double gamma, int ic_mode, double ic_p,
+                  uint32_t t, uint32_t r, uint64_t rng_seed)
+{
+    orc_job jb;
+    memset(&jb, 0, sizeof jb);
+    jb.model = model; jb.row_ptr = row_ptr; jb.col_idx = col_idx;
+    jb.beta = beta; jb.gamma = gamma; jb.ic_mode = ic_mode; jb.ic_p = ic_p;
+    jb.rng_seed = rng_seed;
+    int64_t d = (int64_t)row_ptr[v + 1] - row_ptr[v];
+    jb.kmax = d;
+    jb.surv = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(d + 1));
+    if (!jb.surv) return -2;
+    orc_survival_table(beta, d, jb.surv);
+    jb.g_rec = orc_prob_threshold(gamma);
+    jb.p_const = orc_prob_threshold(ic_p);
+    int s = node_update(&jb, X, v, t, r);
+    free(jb.surv);
+    return s;
+}
