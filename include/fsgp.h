@@ -1,0 +1,190 @@
+/*
+ * fsgp.h -- C ABI of the GB300 batched Monte Carlo graph propagation library.
+ *
+ * One library, libfsgp.so, hand-written CUDA for sm_103a.  It runs the synchronous,
+ * batched Monte Carlo propagation step of FS_GPlib (arXiv 2603.14895) for the SIR,
+ * SIS, Independent Cascade (IC) and Linear Threshold (LT) models:
+ *   - node-synchronous update, every node reads the step-(k-1) states of itself and of
+ *     its in-neighbours and writes its step-k state (Sec. 2, Eq. nodestate; Sec. 3.1,
+ *     Eqs. all / ms / agg / updata);
+ *   - R independent realizations batched along a lane axis (Sec. 3.1, Eq. batch), here
+ *     bit-packed: lane r of a node lives in bit (r & 31) of 32-bit word (r >> 5);
+ *   - the SIR rule of Appendix A.1 (two indicator vectors h, r -> two bit-planes).
+ *
+ * Conventions for every entry point
+ *   - Return value: FSGP_OK (0) or a negative FSGP_E* code.  A human-readable message
+ *     for the last failure of the calling thread is available from fsgp_last_error().
+ *     No C++ exception crosses this boundary.
+ *   - Pointers are plain host or device pointers as the flags say; no framework types.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).  Work
+ *     is enqueued on that stream.  Calls that return results in host memory synchronise
+ *     the stream before returning; calls that return results in device memory do not.
+ *   - Thread safety: distinct graph handles may be used concurrently.  Calls that use
+ *     the same graph handle must not overlap (the handle owns the simulation
+ *     workspace).
+ *
+ * Integer randomness contract (shared by every path; identical results for every
+ * tuning choice and for any split of realizations across GPUs):
+ *   key = (lo32(rng_seed), hi32(rng_seed));  for tag tau, subject a, step t, lane r:
+ *   P_j = Philox4x32-10(key, ctr = (a, t, r >> 5, (tau << 8) | (j >> 2)))[j & 3],
+ *   j = 0..31, and bit (31 - j) of the 32-bit uniform u is bit (r & 31) of P_j.
+ *   Tags: 1 infection (a = node), 2 recovery (a = node), 3 IC arc trial (a = position
+ *   of the arc in the in-CSR column array), 4 LT threshold (a = node, t = 0).
+ *   Philox4x32-10: Salmon, Moraes, Dror, Shaw, SC'11.
+ *
+ * Decision rules (integer readings of the paper; thresholds are built on the host):
+ *   SIR/SIS infection of a susceptible lane with k >= 1 infected in-arcs:
+ *     u >= surv[k], surv[0] = 2^32, surv[k] = floor(surv[k-1] * q / 2^32),
+ *     q = 2^32 - llrint(beta * 2^32)  (probability 1-(1-beta)^k up to k * 2^-32).
+ *   Recovery of an infected lane: u < llrint(gamma * 2^32).
+ *   IC arc (w -> v) tried at the step after w activates, if v is inactive:
+ *     weighted cascade: u * d_in(v) < 2^32; constant: u < llrint(p * 2^32).
+ *   LT: theta = u(tag 4, v, t = 0); an inactive lane with k >= 1 active in-arcs
+ *     activates iff k * 2^32 >= theta * d_in(v).
+ *   In-arcs count with multiplicity (duplicate arcs and self-loops are kept).
+ */
+#ifndef FSGP_H
+#define FSGP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+#define FSGP_OK 0
+#define FSGP_EINVAL (-1)          /* an argument is out of range or inconsistent */
+#define FSGP_ENOMEM (-2)          /* device or host allocation failed */
+#define FSGP_ECUDA (-3)           /* a CUDA runtime call failed (message has details) */
+#define FSGP_ETIMEOUT (-4)        /* a bounded device-side wait ran out */
+#define FSGP_EUNSUPPORTED (-5)    /* a valid request this build does not implement */
+
+/* ------------------------------------------------------------------------ models */
+#define FSGP_SIR 0   /* planes: 0 = I (infected), 1 = R (recovered) */
+#define FSGP_SIS 1   /* planes: 0 = I */
+#define FSGP_IC 2    /* planes: 0 = A (active), 1 = F (activated at the last step) */
+#define FSGP_LT 3    /* planes: 0 = A, 1 = F */
+
+/* Compartments reported in counts / freq / per-realization counts, index 0,1,2:
+ *   SIR: S, I, R.  SIS: S, I, 0.  IC and LT: inactive, newly active (F), active
+ *   before the last step (A and not F). */
+
+/* ------------------------------------------------------------------------- flags */
+#define FSGP_PTR_HOST 0u
+#define FSGP_PTR_DEVICE 1u
+
+#define FSGP_IC_WEIGHTED_CASCADE 0   /* arc probability 1 / d_in(target) */
+#define FSGP_IC_CONSTANT 1           /* arc probability ic_p */
+
+/* Opaque graph handle: owns a device copy of the in-CSR, its out-CSR, the degree
+ * classes used to schedule rows, and the simulation workspace. */
+typedef struct fsgp_graph fsgp_graph;
+
+typedef struct {
+    double beta;      /* SIR/SIS per-arc infection probability, [0, 1] */
+    double gamma;     /* SIR/SIS recovery probability, [0, 1] */
+    int32_t ic_mode;  /* FSGP_IC_WEIGHTED_CASCADE or FSGP_IC_CONSTANT */
+    double ic_p;      /* IC constant arc probability, [0, 1] */
+} fsgp_params;
+
+/* Optional per-kernel profile of one fsgp_simulate call (host struct).  Device times
+ * come from CUDA events recorded around every launch on the call's stream; the call
+ * synchronises that stream before returning when a profile is requested.  Algorithmic
+ * bytes are the bytes each launch is required to move by the method's definition for
+ * the rows it processed: 8 B of row pointers, the node's own state words read and
+ * written (planes x 4 B x words), and per gathered in-arc 4 B of column index plus one
+ * 32-byte sector (or more, for R > 256) of the source's state words. */
+#define FSGP_PROF_KINDS 8
+/* kinds: 0 init, 1 step control, 2 frontier marking, 3 hub chunks, 4 hub finalize,
+ *        5 warp-per-row rows, 6 team-per-row rows, 7 results */
+typedef struct {
+    int64_t launches[FSGP_PROF_KINDS];
+    double ms[FSGP_PROF_KINDS];
+    double alg_bytes[FSGP_PROF_KINDS];
+    int64_t dense_steps;
+    int64_t sparse_steps;
+} fsgp_profile;
+
+/* Tuning and run options.  Zero-initialised = defaults.  No tuning field changes any
+ * result bit; fsgp_autotune() picks the tuning fields. */
+typedef struct {
+    int32_t vector_words;   /* 32-bit state words per thread: 1, 2 or 4 (0 = auto) */
+    int32_t small_max_deg;  /* rows with in-degree <= this: one thread team per row;
+                               rounded down to 2^k - 1 (0 = auto) */
+    int32_t hub_min_deg;    /* rows with in-degree >= this: split over CTAs; rounded down
+                               to a power of two (0 = auto) */
+    int32_t hub_chunk;      /* arcs per CTA for split rows (0 = auto) */
+    double sparse_frac;     /* take the frontier path when the out-arcs of the rows that
+                               push are at most sparse_frac * nnz (0 = auto, <0 = never) */
+    int32_t r_offset;       /* global realization index of lane 0 (multiple of 32) */
+    int32_t t0;             /* absolute index of the starting step (resume) */
+    const uint32_t *init_planes; /* optional start state instead of seeds,
+                               [n_sets][planes][n][ceil(R/32)] u32, same memory kind
+                               as the result buffers (fsgp_result.flags) */
+    fsgp_profile *profile;  /* optional host struct, accumulated (not cleared) */
+    int32_t reserved[8];
+} fsgp_options;
+
+/* Caller-owned result buffers, all host or all device (flags).  NULL = not wanted,
+ * except counts.  W = ceil(R / 32). */
+typedef struct {
+    uint32_t flags;          /* FSGP_PTR_HOST or FSGP_PTR_DEVICE */
+    uint64_t *counts;        /* [n_sets][T+1][3]: compartment totals over all lanes */
+    uint32_t *freq;          /* [n_sets][3][n]: per-node final compartment frequency */
+    uint32_t *per_real;      /* [n_sets][R][T+1][3]: per-realization compartment counts */
+    uint32_t *final_planes;  /* [n_sets][planes][n][W]: final state bit-planes */
+    int32_t *steps_run;      /* [n_sets]: transitions computed (IC/LT stop at the first
+                                step that activates nothing; later rows repeat) */
+} fsgp_result;
+
+/* Create a graph from an int32 in-CSR: row v lists the sources u of arcs u -> v
+ * (pulling from in-neighbours, Sec. 2 paradigm definition; CSR definition of Sec. 2).
+ *   row_ptr: n+1 entries, row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz.
+ *   col_idx: nnz entries in [0, n).  The column order is kept: IC draws are keyed by
+ *            the position of an arc in this array.
+ *   flags:   FSGP_PTR_HOST or FSGP_PTR_DEVICE for both arrays (copied; the caller
+ *            keeps ownership of its arrays).
+ *   1 <= n < 2^31 - 1, 0 <= nnz < 2^31.
+ * On success *out receives a handle released by fsgp_graph_destroy.  Errors: EINVAL for
+ * a malformed CSR (checked on the device), ENOMEM, ECUDA.  Synchronises the stream. */
+int fsgp_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t n,
+                      int64_t nnz, uint32_t flags, void *stream, fsgp_graph **out);
+
+/* Release a graph and its workspace (NULL is accepted).  Synchronises the device. */
+int fsgp_graph_destroy(fsgp_graph *g);
+
+/* Query sizes: any output pointer may be NULL. */
+int fsgp_graph_info(const fsgp_graph *g, int32_t *n, int64_t *nnz, int32_t *max_in_degree,
+                    int64_t *device_bytes);
+
+/* Number of state bit-planes of a model (2 for SIR, IC, LT; 1 for SIS), or EINVAL. */
+int fsgp_model_planes(int32_t model);
+
+/* Run R realizations of `model` for T synchronous steps from each of n_sets seed sets
+ * (paper API: run_epochs(epochs = R, times = T), Sec. 4.2.1).
+ *   seed_nodes/seed_offsets: set s is seed_nodes[seed_offsets[s] .. seed_offsets[s+1]);
+ *     seed_offsets has n_sets+1 entries and is always a HOST array; seed_nodes is host
+ *     or device per seed_flags.  Duplicate seeds are allowed.  All R lanes of a set
+ *     start from the same seeds (I for SIR/SIS, A = F for IC/LT).  Ignored when
+ *     opt->init_planes is set.
+ *   1 <= R <= 4096, 0 <= T, n_sets >= 1, probabilities in [0, 1].
+ *   opt may be NULL (defaults).  out->counts must be non-NULL.
+ * Errors: EINVAL, ENOMEM, ECUDA.  Results land in caller buffers; see fsgp_result. */
+int fsgp_simulate(const fsgp_graph *g, int32_t model, const fsgp_params *params,
+                  const int32_t *seed_nodes, const int64_t *seed_offsets, int32_t n_sets,
+                  uint32_t seed_flags, int32_t R, int32_t T, uint64_t rng_seed,
+                  const fsgp_options *opt, fsgp_result *out, void *stream);
+
+/* Message for the last failure on the calling thread ("" if none).  The pointer stays
+ * valid until the next fsgp_* call on this thread. */
+const char *fsgp_last_error(void);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int fsgp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSGP_H */

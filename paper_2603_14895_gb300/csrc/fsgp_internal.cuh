@@ -1,0 +1,127 @@
+// fsgp_internal.cuh -- device helpers and host-side structures shared by the library's
+// translation units.  Nothing here is part of the C ABI (include/fsgp.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/fsgp.h"
+
+namespace fsgp {
+
+// ----------------------------------------------------------------------- constants
+constexpr uint32_t TAG_INFECT = 1u;
+constexpr uint32_t TAG_RECOVER = 2u;
+constexpr uint32_t TAG_IC_EDGE = 3u;
+constexpr uint32_t TAG_LT_THRESH = 4u;
+constexpr uint64_t TWO32 = 4294967296ull;
+
+constexpr int kBlock = 256;          // threads per CTA for the row kernels
+constexpr int kSmallBits = 8;        // bit-sliced counter width, team-per-row rows (d <= 255)
+constexpr int kWideBits = 16;        // warp-per-row rows and hub chunks (d <= 65535)
+constexpr int kMaxR = 4096;
+
+// list entry flag: the row's source lanes push to its out-neighbours next step
+constexpr uint32_t kPushBit = 0x80000000u;
+
+// ----------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11.
+// Ten rounds of two 32x32->64 multiplies; the high halves are xored with the other
+// counter words and the key; the key advances by the Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        if (i) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Lanes of M whose uniform u(tag, a, t, lane) is below thr (thr may be 2^32 or more =
+// every lane).  The comparison runs MSB first over the bit-planes of u and stops as
+// soon as every lane of M is decided, so most calls need one or two Philox blocks.
+__device__ __forceinline__ uint32_t lanes_u_less(uint32_t M, uint64_t thr, uint32_t a,
+                                                 uint32_t t, uint32_t g, uint32_t tag,
+                                                 uint32_t k0, uint32_t k1) {
+    if (M == 0u || thr == 0ull) return 0u;
+    if (thr >= TWO32) return M;
+    const uint32_t th = (uint32_t)thr;
+    uint32_t lt = 0u, eq = M;
+    for (uint32_t m = 0; m < 8u && eq; ++m) {
+        const uint4 P = philox4x32_10(make_uint4(a, t, g, (tag << 8) | m), k0, k1);
+        const uint32_t p[4] = {P.x, P.y, P.z, P.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int j = (int)m * 4 + i;
+            if ((th >> (31 - j)) & 1u) {
+                lt |= eq & ~p[i];
+                eq &= p[i];
+            } else {
+                eq &= ~p[i];
+            }
+        }
+    }
+    return lt;
+}
+
+// ------------------------------------------------------------------ host structures
+struct ClassInfo {
+    int32_t bucket_count[33];   // rows per degree bucket (0: d=0, b>=1: 2^(b-1)<=d<2^b)
+    int32_t bucket_start[34];   // start of each bucket in rows_sorted (descending order)
+};
+
+struct HubTable {
+    int32_t min_deg = -1;       // table built for this hub threshold and chunk size
+    int32_t chunk = -1;
+    int32_t n_hubs = 0;
+    int64_t n_chunks = 0;
+    int32_t *d_rows = nullptr;        // [n_hubs], aliases the head of rows_sorted (not owned)
+    int64_t *d_chunk_base = nullptr;  // [n_hubs + 1]
+};
+
+struct Workspace {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace fsgp
+
+struct fsgp_graph {
+    int device = 0;
+    int32_t n = 0;
+    int64_t nnz = 0;
+    int32_t max_deg = 0;
+    int32_t max_out_deg = 0;
+    int32_t *row_ptr = nullptr;     // [n+1] in-CSR
+    int32_t *col = nullptr;         // [nnz]
+    int32_t *out_ptr = nullptr;     // [n+1] out-CSR
+    int32_t *out_dst = nullptr;     // [nnz]
+    int32_t *rows_sorted = nullptr; // [n] rows by degree bucket, high buckets first
+    fsgp::ClassInfo cls{};
+    fsgp::HubTable hub{};
+    fsgp::Workspace ws{};
+    int sm_count = 0;
+    size_t device_bytes = 0;
+};
+
+namespace fsgp {
+// thread-local error message
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+}  // namespace fsgp
+
+#define FSGP_CUDA(call)                                              \
+    do {                                                             \
+        cudaError_t _e = (call);                                     \
+        if (_e != cudaSuccess) return ::fsgp::cuda_fail(_e, #call);  \
+    } while (0)

@@ -1,0 +1,8 @@
+// model_lt.cu -- row kernels of the LT model (one translation unit per model so that the
+// template instantiations compile in parallel).
+#include "rows.cuh"
+
+namespace fsgp {
+template int launch_rows<FSGP_LT>(const StepArgs &, const StepLaunch &, cudaStream_t);
+template int occupancy_rows<FSGP_LT>(int, int, size_t, int *, int *);
+}  // namespace fsgp

@@ -1,0 +1,8 @@
+// model_sis.cu -- row kernels of the SIS model (one translation unit per model so that the
+// template instantiations compile in parallel).
+#include "rows.cuh"
+
+namespace fsgp {
+template int launch_rows<FSGP_SIS>(const StepArgs &, const StepLaunch &, cudaStream_t);
+template int occupancy_rows<FSGP_SIS>(int, int, size_t, int *, int *);
+}  // namespace fsgp

@@ -1,0 +1,523 @@
+// rows.cuh -- the row kernels of one propagation step (gather + count + decide + write),
+// templated on the model, the words per thread V and the team width TEAM.  Included by
+// one translation unit per model so that the instantiations compile in parallel.
+#pragma once
+
+#include "step.cuh"
+
+namespace fsgp {
+
+template <int V>
+struct Vec {
+    uint32_t w[V];
+};
+
+template <int V>
+__device__ __forceinline__ Vec<V> ldg_vec(const uint32_t *p) {
+    Vec<V> r;
+    if constexpr (V == 4) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(p));
+        r.w[0] = q.x; r.w[1] = q.y; r.w[2] = q.z; r.w[3] = q.w;
+    } else if constexpr (V == 2) {
+        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(p));
+        r.w[0] = q.x; r.w[1] = q.y;
+    } else {
+        r.w[0] = __ldg(p);
+    }
+    return r;
+}
+
+template <int V>
+__device__ __forceinline__ void st_vec(uint32_t *p, const uint32_t (&w)[V]) {
+    if constexpr (V == 4) {
+        *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else if constexpr (V == 2) {
+        *reinterpret_cast<uint2 *>(p) = make_uint2(w[0], w[1]);
+    } else {
+        *p = w[0];
+    }
+}
+
+template <int MODEL>
+struct ModelTraits {
+    static constexpr int planes = MODEL == FSGP_SIS ? 1 : 2;
+    // plane gathered from in-neighbours: I (SIR/SIS), F (IC), A (LT)
+    static constexpr int src_plane = MODEL == FSGP_IC ? 1 : 0;
+    static constexpr bool counts = MODEL != FSGP_IC;
+};
+
+__device__ __forceinline__ uint64_t ic_threshold(const StepArgs &A, int32_t d) {
+    // weighted cascade: live iff u * d < 2^32  <=>  u < floor((2^32 - 1) / d) + 1
+    if (A.ic_mode == FSGP_IC_WEIGHTED_CASCADE) return d > 0 ? (TWO32 - 1ull) / (uint64_t)d + 1ull : 0ull;
+    return A.p_const;
+}
+
+// Gather the in-arcs [e_begin, e_end) with stride `step` (groups of 4 consecutive arcs)
+// into bit-sliced counters (SIR/SIS/LT) or live-lane masks (IC).
+template <int MODEL, int V, int B>
+__device__ __forceinline__ void gather_arcs(const StepArgs &A, int64_t e_begin, int64_t e_end,
+                                            int64_t step, int w0, const uint32_t (&need)[V],
+                                            uint64_t ic_thr, uint32_t (&c)[V][B],
+                                            uint32_t (&newly)[V]) {
+    const uint32_t *src = A.cur + (size_t)ModelTraits<MODEL>::src_plane * A.plane_words + w0;
+    const size_t Ws = (size_t)A.Ws;
+    for (int64_t e = e_begin; e < e_end; e += step) {
+        int32_t u[4];
+        bool ok[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            ok[j] = e + j < e_end;
+            u[j] = ok[j] ? __ldg(A.col + e + j) : 0;
+        }
+        Vec<V> x[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (ok[j]) {
+                x[j] = ldg_vec<V>(src + (size_t)u[j] * Ws);
+            } else {
+#pragma unroll
+                for (int i = 0; i < V; ++i) x[j].w[i] = 0u;
+            }
+        }
+        if constexpr (ModelTraits<MODEL>::counts) {
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                if (x[0].w[i] | x[1].w[i] | x[2].w[i] | x[3].w[i])
+                    add4<B>(c[i], x[0].w[i], x[1].w[i], x[2].w[i], x[3].w[i]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    const uint32_t m = x[j].w[i] & need[i] & ~newly[i];
+                    if (m)
+                        newly[i] |= lanes_u_less(m, ic_thr, (uint32_t)(e + j), A.t,
+                                                 A.gbase + (uint32_t)(w0 + i), TAG_IC_EDGE,
+                                                 A.key0, A.key1);
+                }
+            }
+        }
+    }
+}
+
+// Row kernel.  WARP_ROW = false: one team per row; true: one warp per row.
+// which: 0 = small rows, 1 = mid rows.
+template <int MODEL, int V, int TEAM, bool WARP_ROW>
+__global__ void __launch_bounds__(kBlock) k_rows(StepArgs A, int which) {
+    extern __shared__ int32_t s_lane[];
+    constexpr int B = WARP_ROW ? kWideBits : kSmallBits;
+    constexpr int TPW = 32 / TEAM;
+    constexpr int P = ModelTraits<MODEL>::planes;
+    const Ctl *C = A.ctl;
+    if (*(volatile const int32_t *)&C->stop) return;
+    const bool sparse = *(volatile const int32_t *)&C->sparse != 0;
+    const int32_t *rows;
+    int64_t nrows;
+    if (sparse) {
+        rows = which ? A.cand_mid : A.cand_small;
+        nrows = (int64_t)((volatile const uint32_t *)C->cand_n)[which];
+    } else {
+        rows = which ? A.rows_mid : A.rows_small;
+        nrows = which ? A.n_mid : A.n_small;
+    }
+    if (nrows == 0) return;
+    const int nl = A.Ws * 32;
+    const bool lanes_on = A.lane_cnt != nullptr;
+    if (lanes_on) {
+        for (int i = threadIdx.x; i < 2 * nl; i += blockDim.x) s_lane[i] = 0;
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int team = lane / TEAM;
+    const int tl = lane % TEAM;
+    const int w0 = tl * V;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr int RPI = WARP_ROW ? 1 : TPW;
+    const int list_slot = A.k & 1;
+    Accum acc;
+
+    for (int64_t base = gwarp * RPI; base < nrows; base += nwarps * RPI) {
+        const int64_t idx = WARP_ROW ? base : base + team;
+        const bool has_row = idx < nrows;
+        const int32_t v = has_row ? __ldg(rows + idx) : 0;
+        uint32_t s0[V], s1[V], vm[V], need[V];
+        {
+            const size_t off = (size_t)v * A.Ws + w0;
+            Vec<V> a = has_row ? ldg_vec<V>(A.cur + off) : Vec<V>{};
+            Vec<V> b{};
+            if (P == 2 && has_row) b = ldg_vec<V>(A.cur + A.plane_words + off);
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                s0[i] = has_row ? a.w[i] : 0u;
+                s1[i] = (P == 2 && has_row) ? b.w[i] : 0u;
+                vm[i] = has_row ? word_valid_mask(A, w0 + i) : 0u;
+                need[i] = MODEL == FSGP_SIR ? (vm[i] & ~s0[i] & ~s1[i]) : (vm[i] & ~s0[i]);
+            }
+        }
+        uint32_t any_need = 0u;
+#pragma unroll
+        for (int i = 0; i < V; ++i) any_need |= need[i];
+#pragma unroll
+        for (int o = 1; o < TEAM; o <<= 1) any_need |= __shfl_xor_sync(0xffffffffu, any_need, o);
+
+        uint32_t c[V][B];
+        uint32_t newly[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            newly[i] = 0u;
+#pragma unroll
+            for (int b = 0; b < B; ++b) c[i][b] = 0u;
+        }
+        int32_t beg = 0, end = 0;
+        if (has_row) {
+            beg = __ldg(A.row_ptr + v);
+            end = __ldg(A.row_ptr + v + 1);
+        }
+        if (any_need) {
+            const uint64_t ic_thr = ic_threshold(A, end - beg);
+            if (WARP_ROW)
+                gather_arcs<MODEL, V, B>(A, (int64_t)beg + 4 * team, end, 4 * TPW, w0, need, ic_thr, c, newly);
+            else
+                gather_arcs<MODEL, V, B>(A, beg, end, 4, w0, need, ic_thr, c, newly);
+        }
+        if (WARP_ROW) {
+            // merge the teams' partial results (the warp is converged here)
+#pragma unroll
+            for (int o = TEAM; o < 32; o <<= 1) {
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    if constexpr (ModelTraits<MODEL>::counts) {
+                        uint32_t d[B];
+#pragma unroll
+                        for (int b = 0; b < B; ++b) d[b] = __shfl_xor_sync(0xffffffffu, c[i][b], o);
+                        add_sliced<B>(c[i], d);
+                    } else {
+                        newly[i] |= __shfl_xor_sync(0xffffffffu, newly[i], o);
+                    }
+                }
+            }
+        }
+        const bool writer = has_row && (!WARP_ROW || team == 0);
+        uint32_t fl = 0u;
+        if (writer) {
+            uint32_t n0[V], n1[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const uint32_t g = A.gbase + (uint32_t)(w0 + i);
+                WordOut o;
+                if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SIS) {
+                    o = update_sir_word<MODEL, B>(A, (uint32_t)v, g, vm[i], s0[i], s1[i], c[i]);
+                } else if constexpr (MODEL == FSGP_IC) {
+                    o.n0 = s0[i] | newly[i];
+                    o.n1 = newly[i];
+                } else {
+                    o = update_lt_word<B>(A, (uint32_t)v, g, vm[i], s0[i], end - beg, c[i]);
+                }
+                n0[i] = o.n0;
+                n1[i] = o.n1;
+                acc.d0 += (long long)__popc(o.n0) - __popc(s0[i]);
+                acc.d1 += (long long)__popc(o.n1) - __popc(s1[i]);
+                if (lanes_on) {
+                    lane_deltas(s_lane, w0 + i, s0[i], o.n0);
+                    if (P == 2) lane_deltas(s_lane + nl, w0 + i, s1[i], o.n1);
+                }
+                if (o.n0 != s0[i] || o.n1 != s1[i]) fl |= 2u;
+                if ((MODEL == FSGP_SIR || MODEL == FSGP_SIS) ? (o.n0 != 0u) : (o.n1 != 0u)) fl |= 1u;
+            }
+            const size_t off = (size_t)v * A.Ws + w0;
+            st_vec<V>(A.nxt + off, n0);
+            if (P == 2) st_vec<V>(A.nxt + A.plane_words + off, n1);
+        }
+#pragma unroll
+        for (int o = 1; o < TEAM; o <<= 1) fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+        const bool leader = writer && tl == 0;
+        const bool want = leader && fl != 0u;
+        if (want && (fl & 1u)) acc.push_deg += (unsigned long long)(__ldg(A.out_ptr + v + 1) - __ldg(A.out_ptr + v));
+        if (A.prof_bytes && leader) acc.bytes += row_bytes(A, P, any_need != 0u, end - beg);
+        list_append(A, want, (int32_t)((uint32_t)v | ((fl & 1u) ? kPushBit : 0u)), list_slot);
+        if (sparse && leader) atomicAnd(&A.bitmap[v >> 5], ~(1u << (v & 31)));
+    }
+    flush_accum(A, acc, list_slot, WARP_ROW ? PK_MID : PK_SMALL);
+    if (lanes_on) flush_lanes(A, s_lane, nl);
+}
+
+// Hub rows, phase 1: one CTA per chunk of in-arcs; per-lane partial counts (IC: live
+// masks) are added into the hub's scratch slot.
+template <int MODEL, int V, int TEAM>
+__global__ void __launch_bounds__(kBlock) k_hub_chunks(StepArgs A) {
+    __shared__ uint32_t s_cnt[kMaxR];
+    constexpr int B = kWideBits;
+    constexpr int TPB = kBlock / TEAM;
+    constexpr int P = ModelTraits<MODEL>::planes;
+    const Ctl *C = A.ctl;
+    if (*(volatile const int32_t *)&C->stop) return;
+    const bool sparse = *(volatile const int32_t *)&C->sparse != 0;
+    const int nl = A.Ws * 32;
+    const int tl = threadIdx.x % TEAM;
+    const int team = threadIdx.x / TEAM;
+    const int lane = threadIdx.x & 31;
+    const int w0 = tl * V;
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) s_cnt[i] = 0u;
+    __syncthreads();
+    for (int64_t item = blockIdx.x; item < A.n_hub_chunks; item += gridDim.x) {
+        int lo = 0, hi = A.n_hubs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(A.hub_chunk_base + mid) <= item) lo = mid; else hi = mid - 1;
+        }
+        const int h = lo;
+        const int32_t v = __ldg(A.hub_rows + h);
+        if (sparse && !((A.bitmap[v >> 5] >> (v & 31)) & 1u)) continue;
+        uint32_t need[V];
+        uint32_t any_need = 0u;
+        {
+            const size_t off = (size_t)v * A.Ws + w0;
+            Vec<V> a = ldg_vec<V>(A.cur + off);
+            Vec<V> b{};
+            if (P == 2) b = ldg_vec<V>(A.cur + A.plane_words + off);
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const uint32_t vm = word_valid_mask(A, w0 + i);
+                need[i] = MODEL == FSGP_SIR ? (vm & ~a.w[i] & ~b.w[i]) : (vm & ~a.w[i]);
+                any_need |= need[i];
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < TEAM; o <<= 1) any_need |= __shfl_xor_sync(0xffffffffu, any_need, o);
+        if (!any_need) continue;   // identical in every team: the row is shared
+        const int32_t rb = __ldg(A.row_ptr + v), re = __ldg(A.row_ptr + v + 1);
+        const int64_t cidx = item - __ldg(A.hub_chunk_base + h);
+        const int64_t beg = (int64_t)rb + cidx * A.hub_chunk;
+        const int64_t end = min((int64_t)re, beg + A.hub_chunk);
+        uint32_t c[V][B];
+        uint32_t newly[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            newly[i] = 0u;
+#pragma unroll
+            for (int b = 0; b < B; ++b) c[i][b] = 0u;
+        }
+        gather_arcs<MODEL, V, B>(A, beg + 4 * team, end, 4 * TPB, w0, need, ic_threshold(A, re - rb), c, newly);
+#pragma unroll
+        for (int o = TEAM; o < 32; o <<= 1) {
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                if constexpr (ModelTraits<MODEL>::counts) {
+                    uint32_t d[B];
+#pragma unroll
+                    for (int b = 0; b < B; ++b) d[b] = __shfl_xor_sync(0xffffffffu, c[i][b], o);
+                    add_sliced<B>(c[i], d);
+                } else {
+                    newly[i] |= __shfl_xor_sync(0xffffffffu, newly[i], o);
+                }
+            }
+        }
+        if (lane < TEAM) {   // team 0 of the warp holds the warp's totals
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const int w = w0 + i;
+                if constexpr (ModelTraits<MODEL>::counts) {
+                    uint32_t nz = any_count<B>(c[i]);
+                    while (nz) {
+                        const int l = __ffs(nz) - 1;
+                        nz &= nz - 1;
+                        uint32_t k = 0u;
+#pragma unroll
+                        for (int b = 0; b < B; ++b) k |= ((c[i][b] >> l) & 1u) << b;
+                        atomicAdd(&s_cnt[w * 32 + l], k);
+                    }
+                } else {
+                    if (newly[i]) atomicOr(&s_cnt[w], newly[i]);
+                }
+            }
+        }
+        if (A.prof_bytes && threadIdx.x == 0) {
+            const unsigned long long src = A.Ws * 4 > 32 ? (unsigned long long)A.Ws * 4ull : 32ull;
+            atomicAdd(&A.prof_bytes[PK_HUB], 8ull + (unsigned long long)P * 4ull * A.Ws +
+                                             (unsigned long long)(end - beg) * (4ull + src));
+        }
+        __syncthreads();
+        uint32_t *slot = A.hub_scratch + (size_t)h * nl;
+        const int lim = ModelTraits<MODEL>::counts ? nl : A.Ws;
+        for (int i = threadIdx.x; i < lim; i += blockDim.x) {
+            const uint32_t x = s_cnt[i];
+            if (x) {
+                if constexpr (ModelTraits<MODEL>::counts) atomicAdd(slot + i, x);
+                else atomicOr(slot + i, x);
+                s_cnt[i] = 0u;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Hub rows, phase 2: one warp per hub row; lane l decides word g0 + l.  The per-lane
+// counts are re-sliced with ballots (32-bit counters), the scratch slot is cleared.
+template <int MODEL>
+__global__ void __launch_bounds__(kBlock) k_hub_finalize(StepArgs A) {
+    extern __shared__ int32_t s_lane[];
+    constexpr int P = ModelTraits<MODEL>::planes;
+    const Ctl *C = A.ctl;
+    if (*(volatile const int32_t *)&C->stop) return;
+    const bool sparse = *(volatile const int32_t *)&C->sparse != 0;
+    const int nl = A.Ws * 32;
+    const bool lanes_on = A.lane_cnt != nullptr;
+    if (lanes_on) {
+        for (int i = threadIdx.x; i < 2 * nl; i += blockDim.x) s_lane[i] = 0;
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int list_slot = A.k & 1;
+    Accum acc;
+    for (int64_t h = gwarp; h < A.n_hubs; h += nwarps) {
+        const int32_t v = __ldg(A.hub_rows + h);
+        const bool cand = !sparse || ((A.bitmap[v >> 5] >> (v & 31)) & 1u);
+        uint32_t fl = 0u;
+        if (cand) {
+            const int32_t d = __ldg(A.row_ptr + v + 1) - __ldg(A.row_ptr + v);
+            uint32_t *slot = A.hub_scratch + (size_t)h * nl;
+            for (int g0 = 0; g0 < A.Ws; g0 += 32) {
+                const int w = g0 + lane;
+                const bool act = w < A.Ws;
+                uint32_t c[32];
+#pragma unroll
+                for (int b = 0; b < 32; ++b) c[b] = 0u;
+                uint32_t newly = 0u;
+                if constexpr (ModelTraits<MODEL>::counts) {
+                    const int nw = min(32, A.Ws - g0);
+                    for (int ww = 0; ww < nw; ++ww) {
+                        const uint32_t kv = slot[(g0 + ww) * 32 + lane];
+                        if (kv) slot[(g0 + ww) * 32 + lane] = 0u;
+#pragma unroll
+                        for (int b = 0; b < 32; ++b) {
+                            const uint32_t bb = __ballot_sync(0xffffffffu, (kv >> b) & 1u);
+                            if (lane == ww) c[b] = bb;
+                        }
+                    }
+                } else {
+                    if (act) {
+                        newly = slot[w];
+                        if (newly) slot[w] = 0u;
+                    }
+                }
+                if (act) {
+                    const size_t off = (size_t)v * A.Ws + w;
+                    const uint32_t s0 = __ldg(A.cur + off);
+                    const uint32_t s1 = P == 2 ? __ldg(A.cur + A.plane_words + off) : 0u;
+                    const uint32_t vm = word_valid_mask(A, w);
+                    const uint32_t g = A.gbase + (uint32_t)w;
+                    WordOut o;
+                    if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SIS) {
+                        o = update_sir_word<MODEL, 32>(A, (uint32_t)v, g, vm, s0, s1, c);
+                    } else if constexpr (MODEL == FSGP_IC) {
+                        const uint32_t nw2 = newly & vm & ~s0;
+                        o.n0 = s0 | nw2;
+                        o.n1 = nw2;
+                    } else {
+                        o = update_lt_word<32>(A, (uint32_t)v, g, vm, s0, d, c);
+                    }
+                    A.nxt[off] = o.n0;
+                    if (P == 2) A.nxt[A.plane_words + off] = o.n1;
+                    acc.d0 += (long long)__popc(o.n0) - __popc(s0);
+                    acc.d1 += (long long)__popc(o.n1) - __popc(s1);
+                    if (lanes_on) {
+                        lane_deltas(s_lane, w, s0, o.n0);
+                        if (P == 2) lane_deltas(s_lane + nl, w, s1, o.n1);
+                    }
+                    if (o.n0 != s0 || o.n1 != s1) fl |= 2u;
+                    if ((MODEL == FSGP_SIR || MODEL == FSGP_SIS) ? (o.n0 != 0u) : (o.n1 != 0u)) fl |= 1u;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+        const bool want = cand && lane == 0 && fl != 0u;
+        if (want && (fl & 1u)) acc.push_deg += (unsigned long long)(__ldg(A.out_ptr + v + 1) - __ldg(A.out_ptr + v));
+        if (A.prof_bytes && cand && lane == 0)
+            acc.bytes += row_bytes(A, P, false, 0) + 2ull * 4ull * 32ull * (unsigned long long)A.Ws;
+        list_append(A, want, (int32_t)((uint32_t)v | ((fl & 1u) ? kPushBit : 0u)), list_slot);
+        if (sparse && cand && lane == 0) atomicAnd(&A.bitmap[v >> 5], ~(1u << (v & 31)));
+    }
+    flush_accum(A, acc, list_slot, PK_HUBFIN);
+    if (lanes_on) flush_lanes(A, s_lane, nl);
+}
+
+// ------------------------------------------------------------------------- launch
+
+template <int MODEL, int V, int TEAM>
+int launch_rows_vt(const StepArgs &A, const StepLaunch &L, cudaStream_t s) {
+    Prof *pr = L.prof;
+    if (L.have_hub) {
+        if (pr) pr->start(PK_HUB, s);
+        k_hub_chunks<MODEL, V, TEAM><<<L.grid_hub, kBlock, 0, s>>>(A);
+        if (pr) { pr->stop(s); pr->start(PK_HUBFIN, s); }
+        k_hub_finalize<MODEL><<<L.grid_fin, kBlock, L.smem_lanes, s>>>(A);
+        if (pr) pr->stop(s);
+    }
+    if (L.have_mid) {
+        if (pr) pr->start(PK_MID, s);
+        k_rows<MODEL, V, TEAM, true><<<L.grid_mid, kBlock, L.smem_lanes, s>>>(A, 1);
+        if (pr) pr->stop(s);
+    }
+    if (L.have_small) {
+        if (pr) pr->start(PK_SMALL, s);
+        k_rows<MODEL, V, TEAM, false><<<L.grid_small, kBlock, L.smem_lanes, s>>>(A, 0);
+        if (pr) pr->stop(s);
+    }
+    return FSGP_OK;
+}
+
+template <int MODEL, int V, int TEAM>
+void occupancy_vt(size_t smem, int *bps_rows, int *bps_hub) {
+    int a = 1, b = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_rows<MODEL, V, TEAM, false>, kBlock, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_hub_chunks<MODEL, V, TEAM>, kBlock, 0);
+    *bps_rows = a < 1 ? 1 : a;
+    *bps_hub = b < 1 ? 1 : b;
+}
+
+#define FSGP_VT_SWITCH(MACRO)                          \
+    switch (V * 100 + TEAM) {                          \
+        case 101: MACRO(1, 1); break;                  \
+        case 102: MACRO(1, 2); break;                  \
+        case 104: MACRO(1, 4); break;                  \
+        case 108: MACRO(1, 8); break;                  \
+        case 116: MACRO(1, 16); break;                 \
+        case 132: MACRO(1, 32); break;                 \
+        case 201: MACRO(2, 1); break;                  \
+        case 401: MACRO(4, 1); break;                  \
+        case 402: MACRO(4, 2); break;                  \
+        case 404: MACRO(4, 4); break;                  \
+        case 408: MACRO(4, 8); break;                  \
+        case 416: MACRO(4, 16); break;                 \
+        case 432: MACRO(4, 32); break;                 \
+        case 202: MACRO(2, 2); break;                  \
+        case 204: MACRO(2, 4); break;                  \
+        case 208: MACRO(2, 8); break;                  \
+        case 216: MACRO(2, 16); break;                 \
+        case 232: MACRO(2, 32); break;                 \
+        default: return fail(FSGP_EINVAL, "unsupported words-per-thread / team combination"); \
+    }
+
+template <int MODEL>
+int launch_rows(const StepArgs &A, const StepLaunch &L, cudaStream_t s) {
+    const int V = L.V, TEAM = L.TEAM;
+#define FSGP_L(v_, t_) launch_rows_vt<MODEL, v_, t_>(A, L, s)
+    FSGP_VT_SWITCH(FSGP_L)
+#undef FSGP_L
+    return FSGP_OK;
+}
+
+template <int MODEL>
+int occupancy_rows(int V, int TEAM, size_t smem, int *bps_rows, int *bps_hub) {
+#define FSGP_O(v_, t_) occupancy_vt<MODEL, v_, t_>(smem, bps_rows, bps_hub)
+    FSGP_VT_SWITCH(FSGP_O)
+#undef FSGP_O
+    return FSGP_OK;
+}
+
+}  // namespace fsgp

@@ -1,0 +1,405 @@
+// step.cuh -- device side of one synchronous propagation step.
+//
+// Paper anchors: node-synchronous update (Sec. 3.1, Eqs. ms / agg / updata): the
+// message of an in-arc is the source's step-(k-1) state, aggregation counts infected
+// (SIR/SIS) or active (LT) in-arcs per realization, or ORs the live arcs (IC), and the
+// update draws the uniforms of Appendix A.1.  Batched Monte Carlo (Eq. batch): 32
+// realizations per 32-bit word, one bit per lane, one plane per indicator vector.
+//
+// Work decomposition (GB300-specific, not from the paper):
+//   * a "team" of TEAM threads covers all Ws words of one node, V words per thread
+//     (128-bit loads when V = 4);
+//   * small rows: one team per row (a warp holds 32/TEAM rows of similar degree, the
+//     rows come bucketed by degree);
+//   * mid rows: one warp per row, arcs interleaved over the warp's teams, counters
+//     merged with xor-shuffles;
+//   * hub rows: arcs cut into chunks, one CTA per chunk; per-lane counts meet in a
+//     scratch array and a finalize pass makes the decisions.
+//   In-arc counts are bit-sliced: counter bit b of 32 lanes is one word, so one
+//   LOP3-style full adder adds 32 lanes at once.
+#pragma once
+
+#include "fsgp_internal.cuh"
+
+#include <vector>
+
+namespace fsgp {
+
+// Control block in device memory, one per simulation.
+struct Ctl {
+    int32_t stop;          // IC/LT: an earlier step activated nothing
+    int32_t steps_done;    // transitions computed so far (relative to t0)
+    int32_t sparse;        // the current step runs on the frontier lists
+    int32_t err;
+    uint32_t list_n[2];    // rows listed for the next step (by step parity)
+    uint64_t push_outdeg[2];
+    uint32_t cand_n[2];    // sparse candidates: 0 = small rows, 1 = mid rows
+    int32_t dense_steps;   // steps run on the full row lists
+    int32_t sparse_steps;  // steps run on the frontier lists
+};
+
+struct StepArgs {
+    // graph
+    const int32_t *__restrict__ row_ptr;
+    const int32_t *__restrict__ col;
+    const int32_t *__restrict__ out_ptr;
+    const int32_t *__restrict__ out_dst;
+    int32_t n;
+    int32_t Ws;            // words per node in the state arrays (power of two)
+    int32_t W;             // words holding valid lanes, ceil(R/32)
+    uint32_t last_mask;    // valid lanes of word W-1
+    uint32_t gbase;        // global word index of word 0 (realization offset / 32)
+    int32_t small_max_deg; // 2^k - 1
+    int32_t hub_min_deg;   // power of two
+    // state: [planes][n][Ws] per buffer
+    const uint32_t *__restrict__ cur;
+    uint32_t *__restrict__ nxt;
+    size_t plane_words;    // n * Ws
+    // model parameters
+    const uint64_t *__restrict__ surv;  // survival table surv[0..surv_last]
+    int32_t surv_last;
+    int32_t ksat;          // first k with surv[k] = 0, or INT32_MAX
+    uint64_t g_rec;        // recovery threshold
+    uint64_t p_const;      // IC constant threshold
+    int32_t ic_mode;
+    uint32_t key0, key1;
+    uint32_t t;            // absolute step index of the step being computed
+    int32_t k;             // relative step index (1..T)
+    // control and accumulators
+    Ctl *ctl;
+    unsigned long long *pc;        // [2] plane popcounts of this step (running totals)
+    int32_t *lane_cnt;             // [2][Wpad*32] running per-lane plane counts, or null
+    // row lists
+    const int32_t *__restrict__ rows_small;
+    const int32_t *__restrict__ rows_mid;
+    int32_t n_small, n_mid;
+    int32_t *cand_small;
+    int32_t *cand_mid;
+    uint32_t *bitmap;
+    const int32_t *__restrict__ list_in;   // rows listed by the previous step
+    int32_t *list_out;                     // rows listed for the next step
+    // hubs
+    const int32_t *__restrict__ hub_rows;
+    const int64_t *__restrict__ hub_chunk_base;
+    int32_t n_hubs;
+    int64_t n_hub_chunks;
+    int32_t hub_chunk;
+    uint32_t *hub_scratch;          // [n_hubs][Ws*32] per-lane counts (IC: [n_hubs][Ws] masks)
+    unsigned long long *prof_bytes; // [8] algorithmic bytes per kernel kind, or null
+};
+
+// profile kinds (fsgp_profile)
+enum { PK_INIT = 0, PK_BEGIN = 1, PK_MARK = 2, PK_HUB = 3, PK_HUBFIN = 4, PK_MID = 5,
+       PK_SMALL = 6, PK_RESULTS = 7 };
+
+// Algorithmic bytes of one row: row pointers, own state read + written, and per
+// gathered in-arc the column index plus the source's state words (at least a sector).
+__device__ __forceinline__ unsigned long long row_bytes(const StepArgs &A, int planes,
+                                                        bool gathered, int64_t deg) {
+    const unsigned long long own = 2ull * planes * 4ull * (unsigned long long)A.Ws;
+    const unsigned long long src = A.Ws * 4 > 32 ? (unsigned long long)A.Ws * 4ull : 32ull;
+    return 8ull + own + (gathered ? (unsigned long long)deg * (4ull + src) : 0ull);
+}
+
+__device__ __forceinline__ uint32_t word_valid_mask(const StepArgs &A, int w) {
+    return w < A.W - 1 ? 0xffffffffu : (w == A.W - 1 ? A.last_mask : 0u);
+}
+
+// ------------------------------------------------------------ bit-sliced counters
+
+// c += x0 + x1 + x2 + x3 (bit-sliced, 32 lanes per word).  Carry-save compression of
+// the four inputs to three bit-planes, then a ripple that stops at the first zero carry.
+template <int B>
+__device__ __forceinline__ void add4(uint32_t (&c)[B], uint32_t x0, uint32_t x1, uint32_t x2,
+                                     uint32_t x3) {
+    const uint32_t sA = x0 ^ x1 ^ x2;
+    const uint32_t cA = (x0 & x1) | (x2 & (x0 ^ x1));
+    const uint32_t s0 = sA ^ x3;
+    const uint32_t cB = sA & x3;
+    const uint32_t s1 = cA ^ cB;
+    const uint32_t s2 = cA & cB;
+    uint32_t carry = c[0] & s0;
+    c[0] ^= s0;
+    uint32_t t = c[1];
+    c[1] = t ^ s1 ^ carry;
+    carry = (t & s1) | (carry & (t ^ s1));
+    t = c[2];
+    c[2] = t ^ s2 ^ carry;
+    carry = (t & s2) | (carry & (t ^ s2));
+#pragma unroll
+    for (int b = 3; b < B; ++b) {
+        if (!carry) break;
+        const uint32_t nc = c[b] & carry;
+        c[b] ^= carry;
+        carry = nc;
+    }
+}
+
+// c += d (both bit-sliced, no overflow by construction)
+template <int B>
+__device__ __forceinline__ void add_sliced(uint32_t (&c)[B], const uint32_t (&d)[B]) {
+    uint32_t carry = 0;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const uint32_t a = c[b], e = d[b];
+        c[b] = a ^ e ^ carry;
+        carry = (a & e) | (carry & (a ^ e));
+    }
+}
+
+// lanes whose count >= K (K < 2^B)
+template <int B>
+__device__ __forceinline__ uint32_t ge_const(const uint32_t (&c)[B], uint32_t K) {
+    uint32_t gt = 0u, eq = 0xffffffffu;
+#pragma unroll
+    for (int b = B - 1; b >= 0; --b) {
+        if ((K >> b) & 1u) {
+            eq &= c[b];
+        } else {
+            gt |= eq & c[b];
+            eq &= ~c[b];
+        }
+    }
+    return gt | eq;
+}
+
+template <int B>
+__device__ __forceinline__ uint32_t any_count(const uint32_t (&c)[B]) {
+    uint32_t a = 0u;
+#pragma unroll
+    for (int b = 0; b < B; ++b) a |= c[b];
+    return a;
+}
+
+// Lanes of `rem` grouped by equal count k; for each group the uniform of the lane is
+// compared with thr(k) MSB first.  The first 8 Philox planes of (tag, a, t, g) (two
+// blocks) are generated once, on first use, and shared by all groups; a group still
+// tied after 8 planes (probability about 2^-8 per lane) generates the rest itself.
+// Returns the lanes with u < thr(k).
+template <int B, class ThrFn>
+__device__ __forceinline__ uint32_t grouped_u_less(const uint32_t (&c)[B], uint32_t rem,
+                                                   ThrFn thr_of, uint32_t a, uint32_t t,
+                                                   uint32_t g, uint32_t tag, uint32_t k0,
+                                                   uint32_t k1) {
+    uint32_t P[8];
+    int ngen = 0;
+    uint32_t res = 0u;
+    while (rem) {
+        const int lane = __ffs(rem) - 1;
+        uint32_t k = 0u;
+#pragma unroll
+        for (int b = 0; b < B; ++b) k |= ((c[b] >> lane) & 1u) << b;
+        uint32_t M = rem;
+#pragma unroll
+        for (int b = 0; b < B; ++b) M &= ((k >> b) & 1u) ? c[b] : ~c[b];
+        rem &= ~M;
+        const uint64_t thr = thr_of(k);
+        if (thr == 0ull) continue;
+        if (thr >= TWO32) {
+            res |= M;
+            continue;
+        }
+        const uint32_t th = (uint32_t)thr;
+        uint32_t lt = 0u, eq = M;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if ((j & 3) == 0) {
+                if (!eq) break;
+                if (ngen <= (j >> 2)) {
+                    const uint4 Q = philox4x32_10(make_uint4(a, t, g, (tag << 8) | (uint32_t)(j >> 2)), k0, k1);
+                    P[j] = Q.x;
+                    P[j + 1] = Q.y;
+                    P[j + 2] = Q.z;
+                    P[j + 3] = Q.w;
+                    ngen = (j >> 2) + 1;
+                }
+            }
+            const uint32_t p = P[j];
+            if ((th >> (31 - j)) & 1u) {
+                lt |= eq & ~p;
+                eq &= p;
+            } else {
+                eq &= ~p;
+            }
+        }
+        for (uint32_t m = 2; m < 8u && eq; ++m) {
+            const uint4 Q = philox4x32_10(make_uint4(a, t, g, (tag << 8) | m), k0, k1);
+            const uint32_t q[4] = {Q.x, Q.y, Q.z, Q.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int j = (int)m * 4 + i;
+                if ((th >> (31 - j)) & 1u) {
+                    lt |= eq & ~q[i];
+                    eq &= q[i];
+                } else {
+                    eq &= ~q[i];
+                }
+            }
+        }
+        res |= lt;
+    }
+    return res;
+}
+
+// ------------------------------------------------------- per-word update (Eq. updata)
+
+struct WordOut {
+    uint32_t n0, n1;
+};
+
+// SIR / SIS word update from counts of infected in-arcs (Appendix A.1 rules).
+template <int MODEL, int B>
+__device__ __forceinline__ WordOut update_sir_word(const StepArgs &A, uint32_t v, uint32_t g,
+                                                   uint32_t vm, uint32_t s0, uint32_t s1,
+                                                   const uint32_t (&c)[B]) {
+    const uint32_t S = vm & ~s0 & ~s1;
+    const uint32_t cand = S & any_count<B>(c);
+    uint32_t infect = 0u;
+    if (cand) {
+        uint32_t sat = 0u;
+        if ((uint64_t)A.ksat < (1ull << B)) sat = ge_const<B>(c, (uint32_t)A.ksat) & cand;
+        const uint32_t rem = cand & ~sat;
+        uint32_t below = 0u;
+        if (rem) {
+            const uint64_t *surv = A.surv;
+            below = grouped_u_less<B>(c, rem, [surv](uint32_t k) { return __ldg(surv + k); }, v,
+                                      A.t, g, TAG_INFECT, A.key0, A.key1);
+        }
+        infect = sat | (rem & ~below);   // infected iff u >= surv[k]
+    }
+    const uint32_t I = s0 & vm;
+    const uint32_t rec = lanes_u_less(I, A.g_rec, v, A.t, g, TAG_RECOVER, A.key0, A.key1);
+    WordOut o;
+    o.n0 = (s0 & ~rec) | infect;
+    o.n1 = MODEL == FSGP_SIR ? (s1 | rec) : 0u;
+    return o;
+}
+
+// LT word update from counts of active in-arcs: activate iff k*2^32 >= theta*d.
+template <int B>
+__device__ __forceinline__ WordOut update_lt_word(const StepArgs &A, uint32_t v, uint32_t g,
+                                                  uint32_t vm, uint32_t s0, int32_t d,
+                                                  const uint32_t (&c)[B]) {
+    const uint32_t cand = vm & ~s0 & any_count<B>(c);
+    uint32_t act = 0u;
+    if (cand) {
+        uint32_t sat = 0u;
+        if ((uint64_t)d < (1ull << B)) sat = ge_const<B>(c, (uint32_t)d) & cand;
+        const uint32_t rem = cand & ~sat;
+        if (rem) {
+            const uint64_t dd = (uint64_t)d;
+            act = grouped_u_less<B>(c, rem,
+                                    [dd](uint32_t k) { return ((uint64_t)k << 32) / dd + 1ull; },
+                                    v, 0u, g, TAG_LT_THRESH, A.key0, A.key1);
+        }
+        act |= sat;
+    }
+    WordOut o;
+    o.n0 = s0 | act;
+    o.n1 = act;
+    return o;
+}
+
+// ----------------------------------------------------------------- step epilogue
+
+// Per-thread running sums, flushed once per CTA.
+struct Accum {
+    long long d0 = 0, d1 = 0;
+    unsigned long long push_deg = 0;
+    unsigned long long bytes = 0;
+};
+
+// per-lane count changes of one word of one plane (s_plane: that plane's counters)
+__device__ __forceinline__ void lane_deltas(int32_t *s_plane, int w, uint32_t olds, uint32_t news) {
+    uint32_t ch = olds ^ news;
+    while (ch) {
+        const int l = __ffs(ch) - 1;
+        ch &= ch - 1;
+        atomicAdd(&s_plane[w * 32 + l], ((news >> l) & 1u) ? 1 : -1);
+    }
+}
+
+__device__ __forceinline__ void flush_accum(const StepArgs &A, Accum acc, int list_slot, int kind) {
+    __shared__ long long s_red[4][kBlock / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.d0 += __shfl_xor_sync(0xffffffffu, acc.d0, o);
+        acc.d1 += __shfl_xor_sync(0xffffffffu, acc.d1, o);
+        acc.push_deg += __shfl_xor_sync(0xffffffffu, acc.push_deg, o);
+        acc.bytes += __shfl_xor_sync(0xffffffffu, acc.bytes, o);
+    }
+    if (lane == 0) {
+        s_red[0][wid] = acc.d0;
+        s_red[1][wid] = acc.d1;
+        s_red[2][wid] = (long long)acc.push_deg;
+        s_red[3][wid] = (long long)acc.bytes;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long a = 0, b = 0, c = 0, d = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            a += s_red[0][i];
+            b += s_red[1][i];
+            c += s_red[2][i];
+            d += s_red[3][i];
+        }
+        if (A.prof_bytes && d) atomicAdd(&A.prof_bytes[kind], (unsigned long long)d);
+        if (a) atomicAdd(&A.pc[0], (unsigned long long)a);
+        if (b) atomicAdd(&A.pc[1], (unsigned long long)b);
+        if (c) atomicAdd((unsigned long long *)&A.ctl->push_outdeg[list_slot], (unsigned long long)c);
+    }
+}
+
+// per-CTA lane counters (shared memory) -> global running lane counts
+__device__ __forceinline__ void flush_lanes(const StepArgs &A, int32_t *s_lane, int nl) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * nl; i += blockDim.x) {
+        const int32_t x = s_lane[i];
+        if (x) atomicAdd(&A.lane_cnt[i], x);
+    }
+}
+
+// Warp-aggregated append of flagged rows to the next step's list.
+__device__ __forceinline__ void list_append(const StepArgs &A, bool want, int32_t entry,
+                                            int list_slot) {
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&A.ctl->list_n[list_slot], (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (want) A.list_out[base + __popc(m & ((1u << lane) - 1u))] = entry;
+}
+
+// Launch shape of the row kernels of one step (host side).
+struct StepLaunch {
+    int V, TEAM;
+    int grid_small, grid_mid, grid_hub, grid_fin;
+    size_t smem_lanes;     // dynamic shared memory for per-lane counters (0 = off)
+    bool have_small, have_mid, have_hub;
+    struct Prof *prof;     // host-side event recorder, or null
+};
+
+// Host-side recorder of CUDA events around launches (fsgp_profile).
+struct Prof {
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind;   // kind of the interval that starts at ev[i]
+    void start(int k, cudaStream_t s) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, s);
+        ev.push_back(e);
+        kind.push_back(k);
+    }
+    void stop(cudaStream_t s) { start(-1, s); }
+};
+
+// Defined in rows.cuh, instantiated once per model (model_*.cu).
+template <int MODEL>
+int launch_rows(const StepArgs &A, const StepLaunch &L, cudaStream_t s);
+template <int MODEL>
+int occupancy_rows(int V, int TEAM, size_t smem, int *bps_rows, int *bps_hub);
+
+}  // namespace fsgp

@@ -1,0 +1,274 @@
+"""Thin Python binding of libfsgp.so (C ABI declared in include/fsgp.h).
+
+Argument marshalling only: every step of the simulation runs in the library's CUDA
+kernels.  PyTorch provides device memory (result tensors) and the CUDA stream.  The
+library is loaded from this package directory; if it is missing it is built with nvcc,
+and if that fails the import fails -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lock = threading.Lock()
+_lib = None
+
+FSGP_OK = 0
+FSGP_EINVAL, FSGP_ENOMEM, FSGP_ECUDA, FSGP_ETIMEOUT, FSGP_EUNSUPPORTED = -1, -2, -3, -4, -5
+SIR, SIS, IC, LT = 0, 1, 2, 3
+PTR_HOST, PTR_DEVICE = 0, 1
+IC_WEIGHTED_CASCADE, IC_CONSTANT = 0, 1
+
+
+class FsgpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"fsgp error {code}: {msg}")
+        self.code = code
+
+
+class fsgp_params(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("ic_mode", ctypes.c_int32), ("ic_p", ctypes.c_double)]
+
+
+class fsgp_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 8), ("ms", ctypes.c_double * 8),
+                ("alg_bytes", ctypes.c_double * 8), ("dense_steps", ctypes.c_int64),
+                ("sparse_steps", ctypes.c_int64)]
+
+
+PROFILE_KINDS = ["init", "step_control", "frontier_mark", "hub_chunks", "hub_finalize",
+                 "rows_warp", "rows_team", "results"]
+
+
+class fsgp_options(ctypes.Structure):
+    _fields_ = [("vector_words", ctypes.c_int32), ("small_max_deg", ctypes.c_int32),
+                ("hub_min_deg", ctypes.c_int32), ("hub_chunk", ctypes.c_int32),
+                ("sparse_frac", ctypes.c_double), ("r_offset", ctypes.c_int32),
+                ("t0", ctypes.c_int32), ("init_planes", ctypes.c_void_p),
+                ("profile", ctypes.POINTER(fsgp_profile)), ("reserved", ctypes.c_int32 * 8)]
+
+
+class fsgp_result(ctypes.Structure):
+    _fields_ = [("flags", ctypes.c_uint32), ("counts", ctypes.c_void_p),
+                ("freq", ctypes.c_void_p), ("per_real", ctypes.c_void_p),
+                ("final_planes", ctypes.c_void_p), ("steps_run", ctypes.c_void_p)]
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "libfsgp.so")
+
+
+def load():
+    """Load libfsgp.so (building it first if absent).  Raises if it cannot be loaded."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            from . import build as _build
+            _build.build()
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        lib.fsgp_graph_create.argtypes = [P, P, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                          P, ctypes.POINTER(P)]
+        lib.fsgp_graph_create.restype = ctypes.c_int
+        lib.fsgp_graph_destroy.argtypes = [P]
+        lib.fsgp_graph_destroy.restype = ctypes.c_int
+        lib.fsgp_graph_info.argtypes = [P, P, P, P, P]
+        lib.fsgp_graph_info.restype = ctypes.c_int
+        lib.fsgp_model_planes.argtypes = [ctypes.c_int32]
+        lib.fsgp_model_planes.restype = ctypes.c_int
+        lib.fsgp_simulate.argtypes = [P, ctypes.c_int32, ctypes.POINTER(fsgp_params), P, P,
+                                      ctypes.c_int32, ctypes.c_uint32, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_uint64,
+                                      ctypes.POINTER(fsgp_options), ctypes.POINTER(fsgp_result), P]
+        lib.fsgp_simulate.restype = ctypes.c_int
+        lib.fsgp_last_error.argtypes = []
+        lib.fsgp_last_error.restype = ctypes.c_char_p
+        lib.fsgp_version.argtypes = []
+        lib.fsgp_version.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != FSGP_OK:
+        raise FsgpError(rc, load().fsgp_last_error().decode())
+
+
+def _ptr(x):
+    """Raw address of a torch tensor, numpy array or None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---------------------------------------------------------------- C-ABI mirrors
+
+def fsgp_last_error() -> str:
+    return load().fsgp_last_error().decode()
+
+
+def fsgp_version() -> int:
+    return load().fsgp_version()
+
+
+def fsgp_model_planes(model: int) -> int:
+    rc = load().fsgp_model_planes(model)
+    if rc < 0:
+        _check(rc)
+    return rc
+
+
+def fsgp_graph_create(row_ptr, col_idx, n: int, nnz: int, flags: int, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().fsgp_graph_create(_ptr(row_ptr), _ptr(col_idx), n, nnz, flags,
+                                    _stream_handle(stream), ctypes.byref(h)))
+    return h
+
+
+def fsgp_graph_destroy(h) -> None:
+    _check(load().fsgp_graph_destroy(h))
+
+
+def fsgp_graph_info(h) -> dict:
+    n = ctypes.c_int32()
+    nnz = ctypes.c_int64()
+    md = ctypes.c_int32()
+    b = ctypes.c_int64()
+    _check(load().fsgp_graph_info(h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(md),
+                                  ctypes.byref(b)))
+    return {"n": n.value, "nnz": nnz.value, "max_in_degree": md.value, "device_bytes": b.value}
+
+
+def fsgp_simulate(h, model, params: fsgp_params, seed_nodes, seed_offsets, n_sets, seed_flags,
+                  R, T, rng_seed, options: fsgp_options | None, result: fsgp_result,
+                  stream=None) -> None:
+    opt = ctypes.byref(options) if options is not None else None
+    _check(load().fsgp_simulate(h, model, ctypes.byref(params), _ptr(seed_nodes),
+                                _ptr(seed_offsets), n_sets, seed_flags, R, T,
+                                ctypes.c_uint64(rng_seed), opt, ctypes.byref(result),
+                                _stream_handle(stream)))
+
+
+# ----------------------------------------------------------- convenience layer
+
+class Graph:
+    """Owns an fsgp_graph handle built from an int32 in-CSR (numpy or torch)."""
+
+    def __init__(self, row_ptr, col_idx, stream=None):
+        import torch
+        if isinstance(row_ptr, np.ndarray):
+            row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+            col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+            flags = PTR_HOST
+        else:
+            assert row_ptr.dtype == torch.int32 and col_idx.dtype == torch.int32
+            row_ptr = row_ptr.contiguous()
+            col_idx = col_idx.contiguous()
+            flags = PTR_DEVICE if row_ptr.is_cuda else PTR_HOST
+        self.n = int(row_ptr.shape[0] - 1)
+        self.nnz = int(col_idx.shape[0])
+        self.handle = fsgp_graph_create(row_ptr, col_idx if self.nnz else None, self.n, self.nnz,
+                                        flags, stream)
+
+    def info(self) -> dict:
+        return fsgp_graph_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            fsgp_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_options(**kw) -> fsgp_options:
+    o = fsgp_options()
+    for k, v in kw.items():
+        if k == "init_planes":
+            o.init_planes = _ptr(v)
+        elif k == "profile":
+            o.profile = ctypes.pointer(v)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def simulate(graph: Graph, model: int, seed_sets, R: int, T: int, rng_seed: int, *, beta=0.0,
+             gamma=0.0, ic_mode=IC_WEIGHTED_CASCADE, ic_p=0.0, freq=True, per_real=False,
+             final_planes=False, steps_run=True, device=True, options=None, stream=None,
+             out=None):
+    """Run fsgp_simulate; results are torch tensors on the current CUDA device
+    (device=True) or numpy arrays (device=False)."""
+    import torch
+    n = graph.n
+    if isinstance(seed_sets, np.ndarray) and seed_sets.ndim == 1:
+        seed_sets = [seed_sets]
+    n_sets = len(seed_sets)
+    offs = np.zeros(n_sets + 1, dtype=np.int64)
+    for i, s in enumerate(seed_sets):
+        offs[i + 1] = offs[i] + len(s)
+    seeds = np.concatenate([np.asarray(s, dtype=np.int32) for s in seed_sets]) if offs[-1] \
+        else np.zeros(1, dtype=np.int32)
+    P = fsgp_model_planes(model)
+    W = (R + 31) // 32
+    T1 = T + 1
+    if out is None:
+        out = {}
+        if device:
+            dev = torch.device("cuda", torch.cuda.current_device())
+            mk = lambda shape, dt: torch.zeros(shape, dtype=dt, device=dev)  # noqa: E731
+            out["counts"] = mk((n_sets, T1, 3), torch.int64)
+            if freq:
+                out["freq"] = mk((n_sets, 3, n), torch.int32)
+            if per_real:
+                out["per_real"] = mk((n_sets, R, T1, 3), torch.int32)
+            if final_planes:
+                out["final_planes"] = mk((n_sets, P, n, W), torch.int32)
+            if steps_run:
+                out["steps_run"] = mk((n_sets,), torch.int32)
+        else:
+            out["counts"] = np.zeros((n_sets, T1, 3), dtype=np.uint64)
+            if freq:
+                out["freq"] = np.zeros((n_sets, 3, n), dtype=np.uint32)
+            if per_real:
+                out["per_real"] = np.zeros((n_sets, R, T1, 3), dtype=np.uint32)
+            if final_planes:
+                out["final_planes"] = np.zeros((n_sets, P, n, W), dtype=np.uint32)
+            if steps_run:
+                out["steps_run"] = np.zeros((n_sets,), dtype=np.int32)
+    res = fsgp_result()
+    res.flags = PTR_DEVICE if device else PTR_HOST
+    res.counts = _ptr(out.get("counts"))
+    res.freq = _ptr(out.get("freq"))
+    res.per_real = _ptr(out.get("per_real"))
+    res.final_planes = _ptr(out.get("final_planes"))
+    res.steps_run = _ptr(out.get("steps_run"))
+    prm = fsgp_params(beta=beta, gamma=gamma, ic_mode=ic_mode, ic_p=ic_p)
+    if isinstance(options, dict):
+        options = make_options(**options)
+    fsgp_simulate(graph.handle, model, prm, seeds, offs, n_sets, PTR_HOST, R, T, rng_seed,
+                  options, res, stream)
+    return out
