@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Benchmark: full Monte Carlo SIR and SIS on the web-scale R-MAT graph.
+
+Workload (one bench step = one full Monte Carlo run of SIR and one of SIS):
+  R-MAT scale 26 (67,108,864 nodes), edge factor 16 (1,073,741,824 arcs, duplicates and
+  self-loops kept), (a, b, c) = (0.57, 0.19, 0.19); beta = 0.01, gamma = 0.05; 0.01%
+  uniformly random seeds (6,710 nodes); R = 256 realizations; T = 100 steps; rng seed 3.
+Metric: edge-realization-steps per second (E * R * T per model, summed), whole job.
+
+Timing: W untimed warm-up steps, then K timed steps bracketed by a barrier and
+cudaDeviceSynchronize, CUDA events on the launching stream, max over ranks.  The graph
+(4.3 GB of arcs) and the state planes (8.6 GB) are far larger than L2, so no flush is
+needed.  SM clocks and throttle reasons are sampled with nvidia-smi during the timed
+region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fsgp|reference]
+
+--impl reference times the CPU oracle (test infrastructure) on a bounded sample of the
+same workload: the paper's method has no runnable reference implementation here.
+Multi-GPU (torchrun): realization sharding, rank i runs lanes with r_offset = 256 i
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SCALE = 26
+R = 256
+T = 100
+BETA, GAMMA = 0.01, 0.05
+RNG_SEED = 3
+MODELS = (0, 1)   # SIR, SIS
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------------ clocks sampler
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------ helpers
+
+def gpu_selector(torch) -> str:
+    """nvidia-smi -i argument for the current CUDA device (its UUID when known)."""
+    try:
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        first = vis.split(",")[torch.cuda.current_device()] if vis else str(torch.cuda.current_device())
+        return first
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2603_14895_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kind: str):
+    """DRAM bytes per launch of a kernel kind from the committed ncu summary, or None
+    if absent or taken on different kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic_rmat26.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    k = d.get("kernels", {}).get(kind)
+    return None if k is None else float(k["dram_bytes_per_launch"])
+
+
+def build_workload(scale: int):
+    import workloads as W
+    t0 = time.time()
+    g = W.rmat26_graph(scale)
+    wl = W.rmat26(W.SIR, g, scale)
+    log(f"[bench] graph R-MAT scale {scale}: n={g.n} nnz={g.nnz} in {time.time() - t0:.1f}s")
+    return g, wl.seed_sets[0]
+
+
+# -------------------------------------------------------------------- reference arm
+
+def run_reference(args, g, seeds, rank):
+    """The CPU oracle on a bounded sample of the workload: n_real realizations of SIR
+    for T_s steps on the full graph, one realization per host core."""
+    import oracle as O
+    if rank != 0:
+        return None
+    cores = os.cpu_count() or 1
+    n_real = cores
+    T_s = 1
+
+    def one_step():
+        t = time.perf_counter()
+        O.simulate(O.SIR, g.row_ptr, g.col_idx, seeds, beta=BETA, gamma=GAMMA, R=R, T=T_s,
+                   rng_seed=RNG_SEED, r_lo=0, n_real=n_real, nthreads=cores,
+                   outputs=("counts",))
+        return time.perf_counter() - t
+
+    for _ in range(args.warmup):
+        one_step()
+    times = [one_step() for _ in range(args.steps)]
+    units = float(g.nnz) * n_real * T_s
+    sec = sum(times) / len(times)
+    value = units / sec
+    sample = (f"SIR, {n_real} realizations x {T_s} steps on the full R-MAT scale-{SCALE} graph "
+              f"({g.nnz} arcs) per step, {cores} threads")
+    return {"impl": "reference", "metric": "edge-realization-steps/sec", "value": value,
+            "unit": "edge-realization-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": workload_config(g, seeds),
+            "cpu_baseline": {"value": value, "unit": "edge-realization-steps/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "edge-realization-steps/s",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def workload_config(g, seeds):
+    return {"workload": f"rmat{SCALE}_sir_sis_full_mc_R{R}_T{T}",
+            "graph": f"R-MAT scale {SCALE}, edge factor 16, (a,b,c)=(0.57,0.19,0.19), "
+                     "duplicates and self-loops kept",
+            "n": g.n, "nnz": g.nnz, "R": R, "T": T, "beta": BETA, "gamma": GAMMA,
+            "seeds": int(len(seeds)), "models": ["SIR", "SIS"], "rng_seed": RNG_SEED,
+            "l2": "inputs larger than L2 (4.3 GB arcs, 8.6 GB state planes); no flush"}
+
+
+def cpu_baseline(g, seeds):
+    import oracle as O
+    cores = os.cpu_count() or 1
+    n_real, T_s = cores, 1
+    t = time.perf_counter()
+    O.simulate(O.SIR, g.row_ptr, g.col_idx, seeds, beta=BETA, gamma=GAMMA, R=R, T=T_s,
+               rng_seed=RNG_SEED, r_lo=0, n_real=n_real, nthreads=cores, outputs=("counts",))
+    sec = time.perf_counter() - t
+    return {"value": float(g.nnz) * n_real * T_s / sec, "unit": "edge-realization-steps/s",
+            "cores": cores, "kind": "oracle",
+            "sample": f"SIR, {n_real} realizations x {T_s} steps on the full graph, "
+                      f"{sec:.1f} s of CPU work"}
+
+
+# ------------------------------------------------------------------------- main
+
+def main():
+    global SCALE
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fsgp", choices=["fsgp", "reference"])
+    ap.add_argument("--scale", type=int, default=SCALE)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    SCALE = args.scale
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        g, seeds = build_workload(SCALE)
+        out = run_reference(args, g, seeds, rank)
+        print(json.dumps(out), flush=True)
+        return
+
+    import numpy as np
+    import torch
+    from paper_2603_14895_gb300 import fsgp
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    g, seeds = build_workload(SCALE)
+    t0 = time.time()
+    graph = fsgp.Graph(g.row_ptr, g.col_idx)
+    torch.cuda.synchronize()
+    log(f"[bench] graph on device in {time.time() - t0:.1f}s: {graph.info()}")
+    r_offset = rank * R
+    stream = torch.cuda.current_stream()
+    outs = {m: fsgp.simulate(graph, m, [seeds], R, T, RNG_SEED, beta=BETA, gamma=GAMMA,
+                             freq=True, device=True,
+                             options=dict(r_offset=r_offset)) for m in MODELS}
+
+    def step(profile=None):
+        for m in MODELS:
+            opts = fsgp.make_options(r_offset=r_offset)
+            if profile is not None:
+                opts.profile = fsgp.ctypes.pointer(profile[m])
+            fsgp.simulate(graph, m, [seeds], R, T, RNG_SEED, beta=BETA, gamma=GAMMA,
+                          device=True, options=opts, out=outs[m])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    profiles = {m: fsgp.fsgp_profile() for m in MODELS}
+    sampler = ClockSampler(gpu_selector(torch))
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(profiles)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    if dist is not None:
+        tt = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_per_step = ms_total / args.steps
+    units_per_step = float(g.nnz) * R * T * len(MODELS)
+    value = units_per_step * world / (ms_per_step / 1e3)
+
+    # per-kernel roofline from the profiled timed region
+    kinds = fsgp.PROFILE_KINDS
+    agg_ms = [sum(profiles[m].ms[i] for m in MODELS) for i in range(8)]
+    agg_b = [sum(profiles[m].alg_bytes[i] for m in MODELS) for i in range(8)]
+    agg_n = [sum(profiles[m].launches[i] for m in MODELS) for i in range(8)]
+    dom = max(range(8), key=lambda i: agg_ms[i])
+    peak, peak_kind = measured_peaks()
+    achieved = (agg_b[dom] / agg_n[dom]) / (agg_ms[dom] / agg_n[dom] / 1e3) / 1e9 if agg_n[dom] else 0.0
+    traffic = ncu_traffic(kinds[dom])
+    launches = sum(profiles[m].kernel_launches for m in MODELS)
+    per_kernel = {kinds[i]: {"launches": agg_n[i] // args.steps,
+                             "ms_per_step": agg_ms[i] / args.steps,
+                             "alg_GBps": (agg_b[i] / (agg_ms[i] / 1e3) / 1e9) if agg_ms[i] else 0.0}
+                  for i in range(8) if agg_n[i]}
+    wall = {}
+    for m, nm in zip(MODELS, ("SIR", "SIS")):
+        wall[nm] = sum(profiles[m].ms) / args.steps / 1e3
+
+    # end to end through the public API with host buffers (graph upload included)
+    e2e = None
+    if not args.no_e2e:
+        rp = torch.from_numpy(g.row_ptr).pin_memory()
+        ci = torch.from_numpy(g.col_idx).pin_memory()
+        sd = torch.from_numpy(seeds.astype(np.int32)).pin_memory()
+        host_out = {m: {"counts": np.zeros((1, T + 1, 3), np.uint64),
+                        "freq": np.zeros((1, 3, g.n), np.uint32)} for m in MODELS}
+        n_e2e = max(1, args.steps)
+        graph.close()
+        torch.cuda.synchronize()
+        barrier()
+        t = time.perf_counter()
+        for _ in range(n_e2e):
+            gh = fsgp.Graph(rp, ci)
+            for m in MODELS:
+                fsgp.simulate(gh, m, [sd.numpy()], R, T, RNG_SEED, beta=BETA, gamma=GAMMA,
+                              device=False, options=dict(r_offset=r_offset), out=host_out[m])
+            gh.close()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t) / n_e2e
+        if dist is not None:
+            tt = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        h2d = g.row_ptr.nbytes + g.col_idx.nbytes + seeds.nbytes * len(MODELS)
+        d2h = sum(v.nbytes for m in MODELS for v in host_out[m].values())
+        e2e = {"value": units_per_step * world / e2e_s, "unit": "edge-realization-steps/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "seconds_per_step": e2e_s}
+        # the host results must equal the device results
+        for m in MODELS:
+            assert np.array_equal(host_out[m]["counts"][0],
+                                  outs[m]["counts"][0].cpu().numpy().astype(np.uint64))
+    else:
+        graph.close()
+
+    result = {
+        "metric": "edge-realization-steps/sec", "value": value,
+        "unit": "edge-realization-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": workload_config(g, seeds),
+        "full_mc_wall_s": wall,
+        "roofline": {"bound": "hbm", "kernel": kinds[dom], "achieved": achieved, "peak": peak,
+                     "peak_source": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak if peak else None, "traffic": traffic},
+        "kernels": per_kernel,
+        "dense_steps": sum(profiles[m].dense_steps for m in MODELS) // args.steps,
+        "sparse_steps": sum(profiles[m].sparse_steps for m in MODELS) // args.steps,
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(g, seeds)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

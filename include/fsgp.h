@@ -104,12 +104,13 @@ typedef struct {
     double alg_bytes[FSGP_PROF_KINDS];
     int64_t dense_steps;
     int64_t sparse_steps;
+    int64_t kernel_launches;   /* every kernel this library launched for the call */
 } fsgp_profile;
 
 /* Tuning and run options.  Zero-initialised = defaults.  No tuning field changes any
  * result bit; fsgp_autotune() picks the tuning fields. */
 typedef struct {
-    int32_t vector_words;   /* 32-bit state words per thread: 1, 2 or 4 (0 = auto) */
+    int32_t vector_words;   /* 32-bit state words per thread: 1, 2 or 4 (0 = auto: 2) */
     int32_t small_max_deg;  /* rows with in-degree <= this: one thread team per row;
                                rounded down to 2^k - 1 (0 = auto) */
     int32_t hub_min_deg;    /* rows with in-degree >= this: split over CTAs; rounded down

@@ -116,8 +116,10 @@ class OracleResult:
 
 def simulate(model: int, row_ptr, col_idx, seeds, *, beta=0.0, gamma=0.0,
              ic_mode=IC_WEIGHTED_CASCADE, ic_p=0.0, R=1, T=0, rng_seed=0,
-             r_lo=0, n_real=None, init_state=None, t0=0, nthreads=None) -> OracleResult:
-    """Run realizations r_lo .. r_lo+n_real-1 of one seed set on the in-CSR graph."""
+             r_lo=0, n_real=None, init_state=None, t0=0, nthreads=None,
+             outputs=("counts", "per_real", "freq", "final_state")) -> OracleResult:
+    """Run realizations r_lo .. r_lo+n_real-1 of one seed set on the in-CSR graph.
+    `outputs` limits which result arrays are produced (counts always are)."""
     lib = _load()
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
     col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
@@ -128,9 +130,9 @@ def simulate(model: int, row_ptr, col_idx, seeds, *, beta=0.0, gamma=0.0,
     if nthreads is None:
         nthreads = os.cpu_count() or 1
     counts = np.zeros((T + 1, 3), dtype=np.uint64)
-    per_real = np.zeros((n_real, T + 1, 3), dtype=np.uint32)
-    freq = np.zeros((3, n), dtype=np.uint32)
-    final_state = np.zeros((n_real, n), dtype=np.uint8)
+    per_real = np.zeros((n_real, T + 1, 3), dtype=np.uint32) if "per_real" in outputs else None
+    freq = np.zeros((3, n), dtype=np.uint32) if "freq" in outputs else None
+    final_state = np.zeros((n_real, n), dtype=np.uint8) if "final_state" in outputs else None
     quiet = np.zeros(n_real, dtype=np.int32)
     if init_state is not None:
         init_state = np.ascontiguousarray(init_state, dtype=np.uint8)

@@ -7,7 +7,7 @@
 
 #include <string>
 
-#include "../../include/fsgp.h"
+#include "fsgp.h"
 
 namespace fsgp {
 
@@ -30,7 +30,8 @@ constexpr uint32_t kPushBit = 0x80000000u;
 // Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11.
 // Ten rounds of two 32x32->64 multiplies; the high halves are xored with the other
 // counter words and the key; the key advances by the Weyl increments between rounds.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+// Not inlined: one copy per kernel keeps the instruction footprint small.
+static __device__ __noinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int i = 0; i < 10; ++i) {
         if (i) {

@@ -178,15 +178,53 @@ __global__ void k_max_out(const int32_t *__restrict__ cnt, int32_t n, int32_t *m
     atomicMax(mx, m);
 }
 
-// Rows grouped by degree bucket, highest bucket first (order inside a bucket is
-// irrelevant to results; rows are independent within a step).
-__global__ void k_bucket_scatter(const int32_t *__restrict__ row_ptr, int32_t n,
-                                 int32_t *cursor /*[33] starts*/, int32_t *rows_sorted) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        const int b = degree_bucket(row_ptr[v + 1] - row_ptr[v]);
-        const int32_t pos = atomicAdd(&cursor[b], 1);
-        rows_sorted[pos] = (int32_t)v;
+// Rows grouped by degree bucket, highest bucket first, and in node order inside a bucket
+// (stable counting sort; node order keeps the state words of a warp's rows close).
+// Phase 1: one warp per chunk of kChunkRows rows counts its rows per bucket, written
+// bucket-major (bucket 32 first) so that one exclusive scan gives every chunk's offsets.
+constexpr int kChunkRows = 1024;
+
+__global__ void k_bucket_chunk_hist(const int32_t *__restrict__ row_ptr, int32_t n,
+                                    int64_t n_chunks, int32_t *hist /*[33][n_chunks]*/) {
+    __shared__ int32_t cnt[8][33];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t chunk = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
+    for (int b = lane; b < 33; b += 32) cnt[wid][b] = 0;
+    __syncwarp();
+    if (chunk < n_chunks) {
+        const int64_t v0 = chunk * kChunkRows;
+        for (int64_t v = v0 + lane; v < min((int64_t)n, v0 + kChunkRows); v += 32)
+            atomicAdd(&cnt[wid][degree_bucket(row_ptr[v + 1] - row_ptr[v])], 1);
+    }
+    __syncwarp();
+    if (chunk < n_chunks)
+        for (int b = lane; b < 33; b += 32) hist[(size_t)(32 - b) * n_chunks + chunk] = cnt[wid][b];
+}
+
+// Phase 2: the same warps place their rows in order at the scanned offsets.
+__global__ void k_bucket_chunk_scatter(const int32_t *__restrict__ row_ptr, int32_t n,
+                                       int64_t n_chunks, const int32_t *__restrict__ off,
+                                       int32_t *rows_sorted) {
+    __shared__ int32_t run[8][33];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t chunk = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
+    if (chunk >= n_chunks) return;
+    for (int b = lane; b < 33; b += 32) run[wid][b] = off[(size_t)(32 - b) * n_chunks + chunk];
+    __syncwarp();
+    const int64_t v0 = chunk * kChunkRows;
+    const int64_t v1 = min((int64_t)n, v0 + kChunkRows);
+    for (int64_t base = v0; base < v1; base += 32) {
+        const int64_t v = base + lane;
+        const bool has = v < v1;
+        const int b = has ? degree_bucket(row_ptr[v + 1] - row_ptr[v]) : 33 + lane;
+        const unsigned same = __match_any_sync(0xffffffffu, b);
+        const int rank = __popc(same & ((1u << lane) - 1u));
+        int32_t pos = 0;
+        if (has) pos = run[wid][b] + rank;
+        __syncwarp();
+        if (has && rank == 0) run[wid][b] += __popc(same);
+        __syncwarp();
+        if (has) rows_sorted[pos] = (int32_t)v;
     }
 }
 
@@ -292,7 +330,7 @@ extern "C" int fsgp_graph_create(const int32_t *row_ptr, const int32_t *col_idx,
             break;
         }
         int32_t *d_err = d_tmp, *d_maxdeg = d_tmp + 1, *d_maxout = d_tmp + 2;
-        int32_t *d_hist = d_tmp + 3, *d_cursor = d_tmp + 36;
+        int32_t *d_hist = d_tmp + 3;
         k_check_rows<<<grid_for(n, 256, g->sm_count), 256, 0, s>>>(g->row_ptr, n, nnz, d_err, d_maxdeg, d_hist);
         int32_t h_head[3];
         if ((e = cudaMemcpyAsync(h_head, d_tmp, sizeof h_head, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
@@ -347,11 +385,36 @@ extern "C" int fsgp_graph_create(const int32_t *row_ptr, const int32_t *col_idx,
             g->cls.bucket_start[b] = start[b];
         }
         g->cls.bucket_start[33] = n;
-        if ((e = cudaMemcpyAsync(d_cursor, start, sizeof(int32_t) * 33, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
-            rc = cuda_fail(e, "cudaMemcpyAsync");
-            break;
+        {
+            // stable bucket order: per-chunk histograms, one scan, ordered placement
+            const int64_t n_chunks = ((int64_t)n + kChunkRows - 1) / kChunkRows;
+            const int64_t hn = 33 * n_chunks;
+            int32_t *d_hist = nullptr, *d_off = nullptr;
+            int64_t *d_t2 = nullptr;
+            const int64_t t2 = (hn + kScanTile - 1) / kScanTile + 1;
+            if ((e = cudaMalloc(&d_hist, sizeof(int32_t) * (size_t)hn)) != cudaSuccess ||
+                (e = cudaMalloc(&d_off, sizeof(int32_t) * (size_t)hn)) != cudaSuccess ||
+                (e = cudaMalloc(&d_t2, sizeof(int64_t) * (size_t)t2)) != cudaSuccess) {
+                cudaFree(d_hist);
+                cudaFree(d_off);
+                rc = cuda_fail(e, "cudaMalloc (bucket sort)");
+                break;
+            }
+            const unsigned blocks = (unsigned)((n_chunks + 7) / 8);
+            k_bucket_chunk_hist<<<blocks, 256, 0, s>>>(g->row_ptr, n, n_chunks, d_hist);
+            rc = exclusive_scan_i32(d_hist, hn, d_off, d_t2, s);
+            if (rc == FSGP_OK)
+                k_bucket_chunk_scatter<<<blocks, 256, 0, s>>>(g->row_ptr, n, n_chunks, d_off, g->rows_sorted);
+            e = cudaStreamSynchronize(s);
+            cudaFree(d_hist);
+            cudaFree(d_off);
+            cudaFree(d_t2);
+            if (rc != FSGP_OK) break;
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "bucket sort");
+                break;
+            }
         }
-        k_bucket_scatter<<<grid_for(n, 256, g->sm_count), 256, 0, s>>>(g->row_ptr, n, d_cursor, g->rows_sorted);
         if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess) {
             rc = cuda_fail(e, "graph build kernels");
             break;

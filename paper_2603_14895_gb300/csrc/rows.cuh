@@ -53,7 +53,9 @@ __device__ __forceinline__ uint64_t ic_threshold(const StepArgs &A, int32_t d) {
 }
 
 // Gather the in-arcs [e_begin, e_end) with stride `step` (groups of 4 consecutive arcs)
-// into bit-sliced counters (SIR/SIS/LT) or live-lane masks (IC).
+// into bit-sliced counters (SIR/SIS/LT) or live-lane masks (IC).  Software pipelined:
+// the column indices of the next group are loaded while the state words of the current
+// group are in flight, so each group costs one memory latency instead of two.
 template <int MODEL, int V, int B>
 __device__ __forceinline__ void gather_arcs(const StepArgs &A, int64_t e_begin, int64_t e_end,
                                             int64_t step, int w0, const uint32_t (&need)[V],
@@ -61,24 +63,23 @@ __device__ __forceinline__ void gather_arcs(const StepArgs &A, int64_t e_begin, 
                                             uint32_t (&newly)[V]) {
     const uint32_t *src = A.cur + (size_t)ModelTraits<MODEL>::src_plane * A.plane_words + w0;
     const size_t Ws = (size_t)A.Ws;
-    for (int64_t e = e_begin; e < e_end; e += step) {
-        int32_t u[4];
-        bool ok[4];
+    int32_t u[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            ok[j] = e + j < e_end;
-            u[j] = ok[j] ? __ldg(A.col + e + j) : 0;
-        }
+    for (int j = 0; j < 4; ++j) u[j] = e_begin + j < e_end ? __ldg(A.col + e_begin + j) : -1;
+    for (int64_t e = e_begin; e < e_end; e += step) {
         Vec<V> x[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            if (ok[j]) {
+            if (u[j] >= 0) {
                 x[j] = ldg_vec<V>(src + (size_t)u[j] * Ws);
             } else {
 #pragma unroll
                 for (int i = 0; i < V; ++i) x[j].w[i] = 0u;
             }
         }
+        const int64_t en = e + step;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) u[j] = en + j < e_end ? __ldg(A.col + en + j) : -1;
         if constexpr (ModelTraits<MODEL>::counts) {
 #pragma unroll
             for (int i = 0; i < V; ++i) {
@@ -103,8 +104,13 @@ __device__ __forceinline__ void gather_arcs(const StepArgs &A, int64_t e_begin, 
 
 // Row kernel.  WARP_ROW = false: one team per row; true: one warp per row.
 // which: 0 = small rows, 1 = mid rows.
+// Resident CTAs per SM the register allocation is bounded for: wider thread words hold
+// more counters, narrower ones run more warps to keep more loads in flight.
+template <int V, bool WIDE>
+constexpr int min_ctas() { return V == 4 ? 2 : (V == 2 ? (WIDE ? 3 : 4) : 4); }
+
 template <int MODEL, int V, int TEAM, bool WARP_ROW>
-__global__ void __launch_bounds__(kBlock) k_rows(StepArgs A, int which) {
+__global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepArgs A, int which) {
     extern __shared__ int32_t s_lane[];
     constexpr int B = WARP_ROW ? kWideBits : kSmallBits;
     constexpr int TPW = 32 / TEAM;
@@ -142,18 +148,17 @@ __global__ void __launch_bounds__(kBlock) k_rows(StepArgs A, int which) {
         const int64_t idx = WARP_ROW ? base : base + team;
         const bool has_row = idx < nrows;
         const int32_t v = has_row ? __ldg(rows + idx) : 0;
-        uint32_t s0[V], s1[V], vm[V], need[V];
+        const size_t off = (size_t)v * A.Ws + w0;
+        // lanes that can change through their in-arcs: S (SIR/SIS) or inactive (IC/LT)
+        uint32_t need[V];
         {
-            const size_t off = (size_t)v * A.Ws + w0;
             Vec<V> a = has_row ? ldg_vec<V>(A.cur + off) : Vec<V>{};
             Vec<V> b{};
-            if (P == 2 && has_row) b = ldg_vec<V>(A.cur + A.plane_words + off);
+            if (MODEL == FSGP_SIR && has_row) b = ldg_vec<V>(A.cur + A.plane_words + off);
 #pragma unroll
             for (int i = 0; i < V; ++i) {
-                s0[i] = has_row ? a.w[i] : 0u;
-                s1[i] = (P == 2 && has_row) ? b.w[i] : 0u;
-                vm[i] = has_row ? word_valid_mask(A, w0 + i) : 0u;
-                need[i] = MODEL == FSGP_SIR ? (vm[i] & ~s0[i] & ~s1[i]) : (vm[i] & ~s0[i]);
+                const uint32_t vm = has_row ? word_valid_mask(A, w0 + i) : 0u;
+                need[i] = MODEL == FSGP_SIR ? (vm & ~a.w[i] & ~b.w[i]) : (vm & ~a.w[i]);
             }
         }
         uint32_t any_need = 0u;
@@ -202,6 +207,19 @@ __global__ void __launch_bounds__(kBlock) k_rows(StepArgs A, int which) {
         const bool writer = has_row && (!WARP_ROW || team == 0);
         uint32_t fl = 0u;
         if (writer) {
+            // own state again (L1/L2-resident): not kept live across the gather
+            uint32_t s0[V], s1[V], vm[V];
+            {
+                Vec<V> a = ldg_vec<V>(A.cur + off);
+                Vec<V> b{};
+                if (P == 2) b = ldg_vec<V>(A.cur + A.plane_words + off);
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    s0[i] = a.w[i];
+                    s1[i] = P == 2 ? b.w[i] : 0u;
+                    vm[i] = word_valid_mask(A, w0 + i);
+                }
+            }
             uint32_t n0[V], n1[V];
 #pragma unroll
             for (int i = 0; i < V; ++i) {
@@ -226,7 +244,6 @@ __global__ void __launch_bounds__(kBlock) k_rows(StepArgs A, int which) {
                 if (o.n0 != s0[i] || o.n1 != s1[i]) fl |= 2u;
                 if ((MODEL == FSGP_SIR || MODEL == FSGP_SIS) ? (o.n0 != 0u) : (o.n1 != 0u)) fl |= 1u;
             }
-            const size_t off = (size_t)v * A.Ws + w0;
             st_vec<V>(A.nxt + off, n0);
             if (P == 2) st_vec<V>(A.nxt + A.plane_words + off, n1);
         }
@@ -246,7 +263,7 @@ __global__ void __launch_bounds__(kBlock) k_rows(StepArgs A, int which) {
 // Hub rows, phase 1: one CTA per chunk of in-arcs; per-lane partial counts (IC: live
 // masks) are added into the hub's scratch slot.
 template <int MODEL, int V, int TEAM>
-__global__ void __launch_bounds__(kBlock) k_hub_chunks(StepArgs A) {
+__global__ void __launch_bounds__(kBlock, min_ctas<V, true>()) k_hub_chunks(StepArgs A) {
     __shared__ uint32_t s_cnt[kMaxR];
     constexpr int B = kWideBits;
     constexpr int TPB = kBlock / TEAM;

@@ -139,11 +139,15 @@ __global__ void k_begin(StepArgs A, int model, unsigned long long sparse_limit, 
     }
     C->steps_done = A.k;
     const int slot = A.k & 1, pslot = (A.k - 1) & 1;
+    C->sparse = (!force_dense && C->list_valid[pslot] && C->push_outdeg[pslot] <= sparse_limit) ? 1 : 0;
+    // The list built now feeds step k+1; when the rows pushing at step k-1 were far
+    // above the frontier limit the next step runs dense anyway, so skip building it.
+    C->build_list = (sparse_limit > 0ull && C->push_outdeg[pslot] <= 4ull * sparse_limit) ? 1 : 0;
+    C->list_valid[slot] = C->build_list;
     C->list_n[slot] = 0u;
     C->push_outdeg[slot] = 0ull;
     C->cand_n[0] = 0u;
     C->cand_n[1] = 0u;
-    C->sparse = (!force_dense && C->push_outdeg[pslot] <= sparse_limit) ? 1 : 0;
     if (C->sparse) C->sparse_steps++; else C->dense_steps++;
 }
 
@@ -403,7 +407,7 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
     while (Ws < W) Ws <<= 1;
     const int P = fsgp_model_planes(model);
     const uint32_t last_mask = (R & 31) ? ((1u << (R & 31)) - 1u) : 0xffffffffu;
-    int V = opt.vector_words ? opt.vector_words : std::min(4, Ws);
+    int V = opt.vector_words ? opt.vector_words : std::min(2, Ws);   // measured best on GB300
     if (V != 1 && V != 2 && V != 4) return fail(FSGP_EINVAL, "vector_words must be 1, 2 or 4");
     if (V > Ws) V = Ws;
     const int TEAM = Ws / V;
@@ -499,6 +503,7 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
     unsigned long long *d_prof = (unsigned long long *)(ws + off[O_PROF]);
     Prof prof;
     const bool profiling = opt.profile != nullptr;
+    int64_t launches = 0;   // kernels launched by this call (profile only)
     FSGP_CUDA(cudaMemcpyAsync(d_surv, surv.data(), sz[O_SURV], cudaMemcpyHostToDevice, s));
 
     // ---------------------------------------------------------------- launch shape
@@ -582,6 +587,11 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
         FSGP_CUDA(cudaMemsetAsync(ws + off[O_STATE], 0, sz[O_STATE], s));
         FSGP_CUDA(cudaMemsetAsync(pc, 0, sz[O_PC], s));
         FSGP_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+        {
+            // the step-0 scan always lists the pushing rows for step 1
+            const int32_t one[3] = {1, 1, 0};
+            FSGP_CUDA(cudaMemcpyAsync(&ctl->build_list, one, sizeof one, cudaMemcpyHostToDevice, s));
+        }
         FSGP_CUDA(cudaMemsetAsync(bitmap, 0, sz[O_BITMAP], s));
         if (lanes) FSGP_CUDA(cudaMemsetAsync(lanes, 0, sz[O_LANES], s));
         if (sz[O_HUB]) FSGP_CUDA(cudaMemsetAsync(hub_scratch, 0, sz[O_HUB], s));
@@ -599,6 +609,7 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
             }
             k_import<<<grid_cap((int64_t)P * n * Ws, 256, g->sm_count, 16), 256, 0, s>>>(
                 src, P, n, W, Ws, last_mask, buf0, buf1);
+            ++launches;
         } else {
             const int64_t ns = seed_offsets[set + 1] - seed_offsets[set];
             const int32_t *sd = seed_nodes + seed_offsets[set];
@@ -610,6 +621,7 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
                 }
                 k_seed<<<grid_cap(ns * Ws, 256, g->sm_count, 16), 256, 0, s>>>(
                     buf0, buf1, A.plane_words, model != FSGP_SIR && model != FSGP_SIS, sd, ns, Ws, W, last_mask);
+                ++launches;
             }
         }
         // step 0
@@ -621,6 +633,7 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
         A.list_in = list[1];
         A.list_out = list[0];
         k_init_scan<<<grid_scan, kBlock, smem_lanes, s>>>(A, model);
+        ++launches;
         if (profiling) prof.stop(s);
         FSGP_CUDA(cudaGetLastError());
         for (int k = 1; k <= T; ++k) {
@@ -643,6 +656,8 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
             }
             rc = launch_rows_model(model, A, L, s);
             if (rc) return rc;
+            launches += 1 + (allow_sparse ? 1 : 0) + (L.have_hub ? 2 : 0) + (L.have_mid ? 1 : 0) +
+                        (L.have_small ? 1 : 0);
         }
         FSGP_CUDA(cudaGetLastError());
         if (profiling) prof.start(PK_RESULTS, s);
@@ -653,6 +668,7 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
         if (planes_d)
             k_export<<<grid_cap((int64_t)P * n * W, 256, g->sm_count, 16), 256, 0, s>>>(A, P, buf0, buf1, planes_d);
         if (profiling) prof.stop(s);
+        launches += 1 + (freq_d ? 1 : 0) + (planes_d ? 1 : 0);
         FSGP_CUDA(cudaGetLastError());
         if (profiling) {
             unsigned long long hb[FSGP_PROF_KINDS];
@@ -674,6 +690,8 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
             for (int i = 0; i < FSGP_PROF_KINDS; ++i) pf->alg_bytes[i] += (double)hb[i];
             pf->dense_steps += hc.dense_steps;
             pf->sparse_steps += hc.sparse_steps;
+            pf->kernel_launches += launches;
+            launches = 0;
         }
         if (host_out) {
             FSGP_CUDA(cudaMemcpyAsync(out->counts + (size_t)set * T1 * 3, counts_d, T1 * 3 * sizeof(uint64_t),

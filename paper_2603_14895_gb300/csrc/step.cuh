@@ -36,6 +36,8 @@ struct Ctl {
     uint32_t cand_n[2];    // sparse candidates: 0 = small rows, 1 = mid rows
     int32_t dense_steps;   // steps run on the full row lists
     int32_t sparse_steps;  // steps run on the frontier lists
+    int32_t build_list;    // the current step lists its rows for the next step
+    int32_t list_valid[2]; // the list of that parity was built
 };
 
 struct StepArgs {
@@ -171,11 +173,68 @@ __device__ __forceinline__ uint32_t any_count(const uint32_t (&c)[B]) {
     return a;
 }
 
-// Lanes of `rem` grouped by equal count k; for each group the uniform of the lane is
-// compared with thr(k) MSB first.  The first 8 Philox planes of (tag, a, t, g) (two
-// blocks) are generated once, on first use, and shared by all groups; a group still
-// tied after 8 planes (probability about 2^-8 per lane) generates the rest itself.
-// Returns the lanes with u < thr(k).
+// Count of one lane, and the lanes of `rem` whose count equals k.
+template <int B>
+__device__ __forceinline__ uint32_t lane_count(const uint32_t (&c)[B], int lane) {
+    uint32_t k = 0u;
+#pragma unroll
+    for (int b = 0; b < B; ++b) k |= ((c[b] >> lane) & 1u) << b;
+    return k;
+}
+
+template <int B>
+__device__ __forceinline__ uint32_t lanes_with_count(const uint32_t (&c)[B], uint32_t rem,
+                                                     uint32_t k) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) rem &= ((k >> b) & 1u) ? c[b] : ~c[b];
+    return rem;
+}
+
+// Largest / smallest count among the lanes of M (M != 0), MSB first.
+template <int B>
+__device__ __forceinline__ uint32_t max_count(const uint32_t (&c)[B], uint32_t M) {
+    uint32_t k = 0u;
+#pragma unroll
+    for (int b = B - 1; b >= 0; --b) {
+        const uint32_t t = M & c[b];
+        if (t) {
+            k |= 1u << b;
+            M = t;
+        }
+    }
+    return k;
+}
+
+template <int B>
+__device__ __forceinline__ uint32_t min_count(const uint32_t (&c)[B], uint32_t M) {
+    uint32_t k = 0u;
+#pragma unroll
+    for (int b = B - 1; b >= 0; --b) {
+        const uint32_t t = M & ~c[b];
+        if (t) M = t;
+        else k |= 1u << b;
+    }
+    return k;
+}
+
+// One MSB-first step of "u < threshold": plane p holds bit (31-j) of u for every lane,
+// tb is bit (31-j) of the threshold.  Lanes leave `eq` at their first differing bit.
+#define FSGP_BIT_STEP(p, tb, lt, eq)  \
+    do {                              \
+        if (tb) {                     \
+            (lt) |= (eq) & ~(p);      \
+            (eq) &= (p);              \
+        } else {                      \
+            (eq) &= ~(p);             \
+        }                             \
+    } while (0)
+
+// Lanes of `rem` whose uniform u(tag, a, t, lane) is below thr(k_lane), k_lane the
+// lane's count.  thr is monotone in k, so every threshold lies between thr(kmin) and
+// thr(kmax) and shares their common binary prefix of L bits: all lanes are first
+// compared with that prefix together, and only lanes still tied after it are resolved
+// group by group (equal k) from bit L on.  The first 8 Philox planes (two blocks) are
+// generated once, on first use; deeper planes are generated where needed.
 template <int B, class ThrFn>
 __device__ __forceinline__ uint32_t grouped_u_less(const uint32_t (&c)[B], uint32_t rem,
                                                    ThrFn thr_of, uint32_t a, uint32_t t,
@@ -184,15 +243,42 @@ __device__ __forceinline__ uint32_t grouped_u_less(const uint32_t (&c)[B], uint3
     uint32_t P[8];
     int ngen = 0;
     uint32_t res = 0u;
-    while (rem) {
-        const int lane = __ffs(rem) - 1;
-        uint32_t k = 0u;
+    int L = 0;
+    uint32_t eq = rem;
+    {
+        const uint64_t ta = thr_of(min_count<B>(c, rem));
+        const uint64_t tb = thr_of(max_count<B>(c, rem));
+        if (ta > 0ull && ta < TWO32 && tb > 0ull && tb < TWO32) {
+            const uint32_t x = (uint32_t)ta ^ (uint32_t)tb;
+            L = x ? __clz(x) : 32;
+            const uint32_t th = (uint32_t)ta;
+            uint32_t lt = 0u;
+            uint4 Q = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-        for (int b = 0; b < B; ++b) k |= ((c[b] >> lane) & 1u) << b;
-        uint32_t M = rem;
-#pragma unroll
-        for (int b = 0; b < B; ++b) M &= ((k >> b) & 1u) ? c[b] : ~c[b];
-        rem &= ~M;
+            for (int j = 0; j < 32; ++j) {
+                if (j >= L || !eq) break;
+                uint32_t p;
+                if (j < 8) {
+                    if ((j & 3) == 0 && ngen <= (j >> 2)) {
+                        const uint4 R = philox4x32_10(make_uint4(a, t, g, (tag << 8) | (uint32_t)(j >> 2)), k0, k1);
+                        P[j] = R.x; P[j + 1] = R.y; P[j + 2] = R.z; P[j + 3] = R.w;
+                        ngen = (j >> 2) + 1;
+                    }
+                    p = P[j];
+                } else {
+                    if ((j & 3) == 0) Q = philox4x32_10(make_uint4(a, t, g, (tag << 8) | (uint32_t)(j >> 2)), k0, k1);
+                    p = (j & 3) == 0 ? Q.x : (j & 3) == 1 ? Q.y : (j & 3) == 2 ? Q.z : Q.w;
+                }
+                FSGP_BIT_STEP(p, (th >> (31 - j)) & 1u, lt, eq);
+            }
+            res = lt;
+            if (L == 32) return res;   // equal thresholds: lanes still tied have u == thr
+        }
+    }
+    while (eq) {
+        const uint32_t k = lane_count<B>(c, __ffs(eq) - 1);
+        const uint32_t M = lanes_with_count<B>(c, eq, k);
+        eq &= ~M;
         const uint64_t thr = thr_of(k);
         if (thr == 0ull) continue;
         if (thr >= TWO32) {
@@ -200,41 +286,26 @@ __device__ __forceinline__ uint32_t grouped_u_less(const uint32_t (&c)[B], uint3
             continue;
         }
         const uint32_t th = (uint32_t)thr;
-        uint32_t lt = 0u, eq = M;
+        uint32_t lt = 0u, e2 = M;
+        uint4 Q = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if ((j & 3) == 0) {
-                if (!eq) break;
+        for (int j = 0; j < 32; ++j) {
+            if (j < L) continue;
+            if (!e2) break;
+            uint32_t p;
+            if (j < 8) {
                 if (ngen <= (j >> 2)) {
-                    const uint4 Q = philox4x32_10(make_uint4(a, t, g, (tag << 8) | (uint32_t)(j >> 2)), k0, k1);
-                    P[j] = Q.x;
-                    P[j + 1] = Q.y;
-                    P[j + 2] = Q.z;
-                    P[j + 3] = Q.w;
+                    const int jb = j & ~3;
+                    const uint4 R = philox4x32_10(make_uint4(a, t, g, (tag << 8) | (uint32_t)(j >> 2)), k0, k1);
+                    P[jb] = R.x; P[jb + 1] = R.y; P[jb + 2] = R.z; P[jb + 3] = R.w;
                     ngen = (j >> 2) + 1;
                 }
-            }
-            const uint32_t p = P[j];
-            if ((th >> (31 - j)) & 1u) {
-                lt |= eq & ~p;
-                eq &= p;
+                p = P[j];
             } else {
-                eq &= ~p;
+                if ((j & 3) == 0 || j == L) Q = philox4x32_10(make_uint4(a, t, g, (tag << 8) | (uint32_t)(j >> 2)), k0, k1);
+                p = (j & 3) == 0 ? Q.x : (j & 3) == 1 ? Q.y : (j & 3) == 2 ? Q.z : Q.w;
             }
-        }
-        for (uint32_t m = 2; m < 8u && eq; ++m) {
-            const uint4 Q = philox4x32_10(make_uint4(a, t, g, (tag << 8) | m), k0, k1);
-            const uint32_t q[4] = {Q.x, Q.y, Q.z, Q.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int j = (int)m * 4 + i;
-                if ((th >> (31 - j)) & 1u) {
-                    lt |= eq & ~q[i];
-                    eq &= q[i];
-                } else {
-                    eq &= ~q[i];
-                }
-            }
+            FSGP_BIT_STEP(p, (th >> (31 - j)) & 1u, lt, e2);
         }
         res |= lt;
     }
@@ -363,6 +434,7 @@ __device__ __forceinline__ void flush_lanes(const StepArgs &A, int32_t *s_lane, 
 // Warp-aggregated append of flagged rows to the next step's list.
 __device__ __forceinline__ void list_append(const StepArgs &A, bool want, int32_t entry,
                                             int list_slot) {
+    if (!*(volatile const int32_t *)&A.ctl->build_list) return;   // uniform per launch
     const unsigned m = __ballot_sync(0xffffffffu, want);
     if (!m) return;
     const int lane = threadIdx.x & 31;

@@ -38,7 +38,7 @@ class fsgp_params(ctypes.Structure):
 class fsgp_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64 * 8), ("ms", ctypes.c_double * 8),
                 ("alg_bytes", ctypes.c_double * 8), ("dense_steps", ctypes.c_int64),
-                ("sparse_steps", ctypes.c_int64)]
+                ("sparse_steps", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
 
 
 PROFILE_KINDS = ["init", "step_control", "frontier_mark", "hub_chunks", "hub_finalize",
