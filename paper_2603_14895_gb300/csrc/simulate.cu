@@ -408,6 +408,7 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
     const int P = fsgp_model_planes(model);
     const uint32_t last_mask = (R & 31) ? ((1u << (R & 31)) - 1u) : 0xffffffffu;
     int V = opt.vector_words ? opt.vector_words : std::min(2, Ws);   // measured best on GB300
+    if (!opt.vector_words && Ws / V > 32) V = Ws / 32;                // R > 2048: 4 words/thread
     if (V != 1 && V != 2 && V != 4) return fail(FSGP_EINVAL, "vector_words must be 1, 2 or 4");
     if (V > Ws) V = Ws;
     const int TEAM = Ws / V;
