@@ -177,6 +177,34 @@ int fsgp_simulate(const fsgp_graph *g, int32_t model, const fsgp_params *params,
                   uint32_t seed_flags, int32_t R, int32_t T, uint64_t rng_seed,
                   const fsgp_options *opt, fsgp_result *out, void *stream);
 
+/* One synchronous step (Eq. nodestate) of `model` that allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code running inside a stream capture or a pre-built CUDA graph, a
+ * process that has handed its free device memory to its own pool, or a runtime that
+ * forbids allocation on its hot path.  It needs no graph handle.
+ *   row_ptr, col_idx: device in-CSR as for fsgp_graph_create (not validated here).
+ *   cur_planes: device input state, next_planes: device output state (must not alias),
+ *     both [planes][n][Ws] u32 with Ws = the smallest power of two >= ceil(R/32);
+ *     padding words and lanes >= R must be zero in cur_planes.
+ *   t: absolute index of the step computed (the Philox counter; IC/LT apply no stop
+ *     rule to a single step).  Lanes are realizations 0..R-1.
+ *   plane_counts: device u64[2], set lanes of each plane of next_planes.
+ *   Results equal those of fsgp_simulate run for one step from the same planes.
+ * Every row takes the CTA-split path: per-lane partial counts of each row meet in a
+ * scratch array that is a fixed 32 MiB device array inside the library, held by every
+ * GPU that loads the library until the process exits.  Limits, checked before any
+ * work (EINVAL with a message): n * 128 * Ws bytes plus about 1.1 MB of tables must fit
+ * the 32 MiB; for SIR/SIS the in-degree may not exceed 65536 unless the survival table
+ * reaches zero earlier (beta not tiny).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it: make that first call
+ * before any stream capture.  Every call shares the array and clears it; calls that
+ * overlap on the GPU race, so order them (one stream, or events).  The call reads the
+ * chunk count back and therefore synchronises `stream` once.  Errors: EINVAL, ECUDA. */
+int fsgp_step_noalloc(int32_t model, const fsgp_params *params, const int32_t *row_ptr,
+                      const int32_t *col_idx, int32_t n, int64_t nnz, int32_t R, uint32_t t,
+                      uint64_t rng_seed, const uint32_t *cur_planes, uint32_t *next_planes,
+                      uint64_t *plane_counts, void *stream);
+
 /* Message for the last failure on the calling thread ("" if none).  The pointer stays
  * valid until the next fsgp_* call on this thread. */
 const char *fsgp_last_error(void);

@@ -529,6 +529,24 @@ int launch_rows(const StepArgs &A, const StepLaunch &L, cudaStream_t s) {
     return FSGP_OK;
 }
 
+// Only the CTA-split pair (chunks, then finalize), for callers that treat every row as
+// a split row.
+template <int MODEL, int V, int TEAM>
+int launch_split_vt(const StepArgs &A, int grid_chunks, int grid_fin, cudaStream_t s) {
+    k_hub_chunks<MODEL, V, TEAM><<<grid_chunks, kBlock, 0, s>>>(A);
+    k_hub_finalize<MODEL><<<grid_fin, kBlock, 0, s>>>(A);
+    return FSGP_OK;
+}
+
+template <int MODEL>
+int launch_split_rows(const StepArgs &A, int V, int TEAM, int grid_chunks, int grid_fin,
+                      cudaStream_t s) {
+#define FSGP_S(v_, t_) launch_split_vt<MODEL, v_, t_>(A, grid_chunks, grid_fin, s)
+    FSGP_VT_SWITCH(FSGP_S)
+#undef FSGP_S
+    return FSGP_OK;
+}
+
 template <int MODEL>
 int occupancy_rows(int V, int TEAM, size_t smem, int *bps_rows, int *bps_hub) {
 #define FSGP_O(v_, t_) occupancy_vt<MODEL, v_, t_>(smem, bps_rows, bps_hub)

@@ -473,5 +473,8 @@ template <int MODEL>
 int launch_rows(const StepArgs &A, const StepLaunch &L, cudaStream_t s);
 template <int MODEL>
 int occupancy_rows(int V, int TEAM, size_t smem, int *bps_rows, int *bps_hub);
+template <int MODEL>
+int launch_split_rows(const StepArgs &A, int V, int TEAM, int grid_chunks, int grid_fin,
+                      cudaStream_t s);
 
 }  // namespace fsgp

@@ -89,6 +89,10 @@ def load():
                                       ctypes.c_int32, ctypes.c_uint64,
                                       ctypes.POINTER(fsgp_options), ctypes.POINTER(fsgp_result), P]
         lib.fsgp_simulate.restype = ctypes.c_int
+        lib.fsgp_step_noalloc.argtypes = [ctypes.c_int32, ctypes.POINTER(fsgp_params), P, P,
+                                          ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.c_uint32, ctypes.c_uint64, P, P, P, P]
+        lib.fsgp_step_noalloc.restype = ctypes.c_int
         lib.fsgp_last_error.argtypes = []
         lib.fsgp_last_error.restype = ctypes.c_char_p
         lib.fsgp_version.argtypes = []
@@ -166,6 +170,16 @@ def fsgp_simulate(h, model, params: fsgp_params, seed_nodes, seed_offsets, n_set
                                 _ptr(seed_offsets), n_sets, seed_flags, R, T,
                                 ctypes.c_uint64(rng_seed), opt, ctypes.byref(result),
                                 _stream_handle(stream)))
+
+
+def fsgp_step_noalloc(model, params: fsgp_params, row_ptr, col_idx, n, nnz, R, t, rng_seed,
+                      cur_planes, next_planes, plane_counts, stream=None) -> None:
+    """One synchronous step with no device allocation (see include/fsgp.h): for callers
+    that cannot call cudaMalloc.  All array arguments are device tensors."""
+    _check(load().fsgp_step_noalloc(model, ctypes.byref(params), _ptr(row_ptr), _ptr(col_idx),
+                                    n, nnz, R, t, ctypes.c_uint64(rng_seed), _ptr(cur_planes),
+                                    _ptr(next_planes), _ptr(plane_counts),
+                                    _stream_handle(stream)))
 
 
 # ----------------------------------------------------------- convenience layer
