@@ -37,6 +37,7 @@ constexpr size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kOffCtl = 0;
 constexpr size_t kOffPc = 256;            // 2 x u64 plane popcounts
 constexpr size_t kOffInfo = 512;          // u64 info[4]: max in-degree, chunks, k_sat
+constexpr size_t kOffSet = 768;           // SetParams of the single set
 constexpr size_t kOffSurv = 1024;         // (kSurvCap + 1) x u64
 constexpr size_t kOffRows = kOffSurv + a256(sizeof(uint64_t) * (kSurvCap + 1));
 
@@ -202,7 +203,7 @@ extern "C" int fsgp_step_noalloc(int32_t model, const fsgp_params *params, const
     uint32_t *slots = (uint32_t *)(base + off_slots);
 
     // the array keeps the last call's contents: clear what must start at zero
-    FSGP_CUDA(cudaMemsetAsync(base, 0, kOffSurv, s));
+    FSGP_CUDA(cudaMemsetAsync(base, 0, kOffSet, s));
     FSGP_CUDA(cudaMemsetAsync(slots, 0, sizeof(uint32_t) * (size_t)n * nl, s));
     const int grid = (int)std::min<int64_t>((int64_t)sm_count * 8, ((int64_t)n + 255) / 256);
     k_na_prep<<<std::max(grid, 1), 256, 0, s>>>(row_ptr, n, rows, chunk_base, info, cur_planes, P, Ws, pc);
@@ -222,6 +223,22 @@ extern "C" int fsgp_step_noalloc(int32_t model, const fsgp_params *params, const
                                      "for this beta");
     }
 
+    SetParams hp{};
+    hp.key0 = (uint32_t)(rng_seed & 0xffffffffu);
+    hp.key1 = (uint32_t)(rng_seed >> 32);
+    hp.surv = surv;
+    hp.ksat = ksat;
+    hp.W = W;
+    hp.last_mask = (R & 31) ? ((1u << (R & 31)) - 1u) : 0xffffffffu;
+    hp.R = R;
+    hp.g_rec = (uint64_t)llrint(params->gamma * 4294967296.0);
+    hp.p_const = (uint64_t)llrint(params->ic_p * 4294967296.0);
+    SetParams *d_sp = (SetParams *)(base + kOffSet);
+    FSGP_CUDA(cudaMemcpyAsync(d_sp, &hp, sizeof hp, cudaMemcpyHostToDevice, s));
+    const int V = std::min(2, Ws);
+    const int SW = std::min(32 * V, Ws);
+    const int TEAM = SW / V;
+
     StepArgs A{};
     A.row_ptr = row_ptr;
     A.col = col_idx;
@@ -229,20 +246,16 @@ extern "C" int fsgp_step_noalloc(int32_t model, const fsgp_params *params, const
     A.out_dst = nullptr;
     A.n = n;
     A.Ws = Ws;
-    A.W = W;
-    A.last_mask = (R & 31) ? ((1u << (R & 31)) - 1u) : 0xffffffffu;
+    A.ws_shift = __builtin_ctz((unsigned)Ws);
+    A.S = 1;
+    A.Wn = Ws;
+    A.nslices = Ws / SW;
     A.gbase = 0;
     A.cur = cur_planes;
     A.nxt = next_planes;
     A.plane_words = (size_t)n * Ws;
-    A.surv = surv;
-    A.surv_last = (int32_t)std::min<int64_t>(max_deg, kSurvCap);
-    A.ksat = ksat;
-    A.g_rec = (uint64_t)llrint(params->gamma * 4294967296.0);
-    A.p_const = (uint64_t)llrint(params->ic_p * 4294967296.0);
+    A.sp = d_sp;
     A.ic_mode = params->ic_mode;
-    A.key0 = (uint32_t)(rng_seed & 0xffffffffu);
-    A.key1 = (uint32_t)(rng_seed >> 32);
     A.t = t;
     A.k = 1;
     A.ctl = ctl;
@@ -253,9 +266,7 @@ extern "C" int fsgp_step_noalloc(int32_t model, const fsgp_params *params, const
     A.n_hub_chunks = n_chunks;
     A.hub_chunk = kNoAllocChunk;
     A.hub_scratch = slots;
-    const int V = Ws > 64 ? 4 : std::min(2, Ws);
-    const int TEAM = Ws / V;
-    const int gc = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count * 4, n_chunks));
+    const int gc = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count * 4, n_chunks * A.nslices));
     const int gf = (int)std::max<int64_t>(1, ((int64_t)n + (kBlock / 32) - 1) / (kBlock / 32));
     rc = launch_split_model(model, A, V, TEAM, gc, gf, s);
     if (rc) return rc;

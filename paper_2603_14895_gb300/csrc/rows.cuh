@@ -46,10 +46,11 @@ struct ModelTraits {
     static constexpr bool counts = MODEL != FSGP_IC;
 };
 
-__device__ __forceinline__ uint64_t ic_threshold(const StepArgs &A, int32_t d) {
-    // weighted cascade: live iff u * d < 2^32  <=>  u < floor((2^32 - 1) / d) + 1
+// IC live-arc threshold of a word: weighted cascade (live iff u * d < 2^32, i.e.
+// u < floor((2^32 - 1) / d) + 1) or the set's constant probability.
+__device__ __forceinline__ uint64_t ic_threshold(const StepArgs &A, int s, int32_t d) {
     if (A.ic_mode == FSGP_IC_WEIGHTED_CASCADE) return d > 0 ? (TWO32 - 1ull) / (uint64_t)d + 1ull : 0ull;
-    return A.p_const;
+    return __ldg(&A.sp[s].p_const);
 }
 
 // Gather the in-arcs [e_begin, e_end) with stride `step` (groups of 4 consecutive arcs)
@@ -59,22 +60,22 @@ __device__ __forceinline__ uint64_t ic_threshold(const StepArgs &A, int32_t d) {
 template <int MODEL, int V, int B>
 __device__ __forceinline__ void gather_arcs(const StepArgs &A, int64_t e_begin, int64_t e_end,
                                             int64_t step, int w0, const uint32_t (&need)[V],
-                                            uint64_t ic_thr, uint32_t (&c)[V][B],
-                                            uint32_t (&newly)[V]) {
+                                            const uint64_t (&ic_thr)[V], const WordCtx (&x)[V],
+                                            uint32_t (&c)[V][B], uint32_t (&newly)[V]) {
     const uint32_t *src = A.cur + (size_t)ModelTraits<MODEL>::src_plane * A.plane_words + w0;
-    const size_t Ws = (size_t)A.Ws;
+    const size_t Wn = (size_t)A.Wn;
     int32_t u[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) u[j] = e_begin + j < e_end ? __ldg(A.col + e_begin + j) : -1;
     for (int64_t e = e_begin; e < e_end; e += step) {
-        Vec<V> x[4];
+        Vec<V> xs[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (u[j] >= 0) {
-                x[j] = ldg_vec<V>(src + (size_t)u[j] * Ws);
+                xs[j] = ldg_vec<V>(src + (size_t)u[j] * Wn);
             } else {
 #pragma unroll
-                for (int i = 0; i < V; ++i) x[j].w[i] = 0u;
+                for (int i = 0; i < V; ++i) xs[j].w[i] = 0u;
             }
         }
         const int64_t en = e + step;
@@ -83,37 +84,39 @@ __device__ __forceinline__ void gather_arcs(const StepArgs &A, int64_t e_begin, 
         if constexpr (ModelTraits<MODEL>::counts) {
 #pragma unroll
             for (int i = 0; i < V; ++i) {
-                if (x[0].w[i] | x[1].w[i] | x[2].w[i] | x[3].w[i])
-                    add4<B>(c[i], x[0].w[i], x[1].w[i], x[2].w[i], x[3].w[i]);
+                if (xs[0].w[i] | xs[1].w[i] | xs[2].w[i] | xs[3].w[i])
+                    add4<B>(c[i], xs[0].w[i], xs[1].w[i], xs[2].w[i], xs[3].w[i]);
             }
         } else {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
 #pragma unroll
                 for (int i = 0; i < V; ++i) {
-                    const uint32_t m = x[j].w[i] & need[i] & ~newly[i];
+                    const uint32_t m = xs[j].w[i] & need[i] & ~newly[i];
                     if (m)
-                        newly[i] |= lanes_u_less(m, ic_thr, (uint32_t)(e + j), A.t,
-                                                 A.gbase + (uint32_t)(w0 + i), TAG_IC_EDGE,
-                                                 A.key0, A.key1);
+                        newly[i] |= lanes_u_less(m, ic_thr[i], (uint32_t)(e + j), A.t, x[i].g,
+                                                 TAG_IC_EDGE, x[i].k0, x[i].k1);
                 }
             }
         }
     }
 }
 
-// Row kernel.  WARP_ROW = false: one team per row; true: one warp per row.
-// which: 0 = small rows, 1 = mid rows.
 // Resident CTAs per SM the register allocation is bounded for: wider thread words hold
 // more counters, narrower ones run more warps to keep more loads in flight.
 template <int V, bool WIDE>
 constexpr int min_ctas() { return V == 4 ? 2 : (V == 2 ? (WIDE ? 3 : 4) : 4); }
 
+// Row kernel: one work item is one slice (TEAM*V words) of one row.
+// WARP_ROW = false: one team per item; true: one warp per item.
+// which: 0 = small rows, 1 = mid rows.
 template <int MODEL, int V, int TEAM, bool WARP_ROW>
 __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepArgs A, int which) {
     extern __shared__ int32_t s_lane[];
+    __shared__ unsigned long long s_pc[2 * kMaxSets];
     constexpr int B = WARP_ROW ? kWideBits : kSmallBits;
     constexpr int TPW = 32 / TEAM;
+    constexpr int SW = TEAM * V;
     constexpr int P = ModelTraits<MODEL>::planes;
     const Ctl *C = A.ctl;
     if (*(volatile const int32_t *)&C->stop) return;
@@ -128,27 +131,35 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
         nrows = which ? A.n_mid : A.n_small;
     }
     if (nrows == 0) return;
-    const int nl = A.Ws * 32;
+    const int nl = A.Wn * 32;
     const bool lanes_on = A.lane_cnt != nullptr;
-    if (lanes_on) {
+    if (lanes_on)
         for (int i = threadIdx.x; i < 2 * nl; i += blockDim.x) s_lane[i] = 0;
-        __syncthreads();
-    }
+    set_acc_zero(s_pc, A.S);
     const int lane = threadIdx.x & 31;
     const int team = lane / TEAM;
     const int tl = lane % TEAM;
-    const int w0 = tl * V;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     constexpr int RPI = WARP_ROW ? 1 : TPW;
     const int list_slot = A.k & 1;
+    const int64_t nitems = nrows * A.nslices;
     Accum acc;
 
-    for (int64_t base = gwarp * RPI; base < nrows; base += nwarps * RPI) {
-        const int64_t idx = WARP_ROW ? base : base + team;
-        const bool has_row = idx < nrows;
-        const int32_t v = has_row ? __ldg(rows + idx) : 0;
-        const size_t off = (size_t)v * A.Ws + w0;
+    for (int64_t base = gwarp * RPI; base < nitems; base += nwarps * RPI) {
+        const int64_t item = WARP_ROW ? base : base + team;
+        const bool has_row = item < nitems;
+        const int64_t ridx = has_row ? item / A.nslices : 0;
+        const int slice = has_row ? (int)(item - ridx * A.nslices) : 0;
+        const int32_t v = has_row ? __ldg(rows + ridx) : 0;
+        const int w0 = slice * SW + tl * V;
+        const size_t off = (size_t)v * A.Wn + w0;
+        WordCtx x[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            x[i] = word_ctx(A, w0 + i);
+            if (!has_row) x[i].vm = 0u;
+        }
         // lanes that can change through their in-arcs: S (SIR/SIS) or inactive (IC/LT)
         uint32_t need[V];
         {
@@ -156,10 +167,8 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
             Vec<V> b{};
             if (MODEL == FSGP_SIR && has_row) b = ldg_vec<V>(A.cur + A.plane_words + off);
 #pragma unroll
-            for (int i = 0; i < V; ++i) {
-                const uint32_t vm = has_row ? word_valid_mask(A, w0 + i) : 0u;
-                need[i] = MODEL == FSGP_SIR ? (vm & ~a.w[i] & ~b.w[i]) : (vm & ~a.w[i]);
-            }
+            for (int i = 0; i < V; ++i)
+                need[i] = MODEL == FSGP_SIR ? (x[i].vm & ~a.w[i] & ~b.w[i]) : (x[i].vm & ~a.w[i]);
         }
         uint32_t any_need = 0u;
 #pragma unroll
@@ -181,11 +190,14 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
             end = __ldg(A.row_ptr + v + 1);
         }
         if (any_need) {
-            const uint64_t ic_thr = ic_threshold(A, end - beg);
+            uint64_t ic_thr[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i)
+                ic_thr[i] = ModelTraits<MODEL>::counts ? 0ull : ic_threshold(A, x[i].s, end - beg);
             if (WARP_ROW)
-                gather_arcs<MODEL, V, B>(A, (int64_t)beg + 4 * team, end, 4 * TPW, w0, need, ic_thr, c, newly);
+                gather_arcs<MODEL, V, B>(A, (int64_t)beg + 4 * team, end, 4 * TPW, w0, need, ic_thr, x, c, newly);
             else
-                gather_arcs<MODEL, V, B>(A, beg, end, 4, w0, need, ic_thr, c, newly);
+                gather_arcs<MODEL, V, B>(A, beg, end, 4, w0, need, ic_thr, x, c, newly);
         }
         if (WARP_ROW) {
             // merge the teams' partial results (the warp is converged here)
@@ -208,7 +220,7 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
         uint32_t fl = 0u;
         if (writer) {
             // own state again (L1/L2-resident): not kept live across the gather
-            uint32_t s0[V], s1[V], vm[V];
+            uint32_t s0[V], s1[V];
             {
                 Vec<V> a = ldg_vec<V>(A.cur + off);
                 Vec<V> b{};
@@ -217,26 +229,24 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
                 for (int i = 0; i < V; ++i) {
                     s0[i] = a.w[i];
                     s1[i] = P == 2 ? b.w[i] : 0u;
-                    vm[i] = word_valid_mask(A, w0 + i);
                 }
             }
             uint32_t n0[V], n1[V];
 #pragma unroll
             for (int i = 0; i < V; ++i) {
-                const uint32_t g = A.gbase + (uint32_t)(w0 + i);
                 WordOut o;
                 if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SIS) {
-                    o = update_sir_word<MODEL, B>(A, (uint32_t)v, g, vm[i], s0[i], s1[i], c[i]);
+                    o = update_sir_word<MODEL, B>(A, (uint32_t)v, x[i], s0[i], s1[i], c[i]);
                 } else if constexpr (MODEL == FSGP_IC) {
                     o.n0 = s0[i] | newly[i];
                     o.n1 = newly[i];
                 } else {
-                    o = update_lt_word<B>(A, (uint32_t)v, g, vm[i], s0[i], end - beg, c[i]);
+                    o = update_lt_word<B>(A, (uint32_t)v, x[i], s0[i], end - beg, c[i]);
                 }
                 n0[i] = o.n0;
                 n1[i] = o.n1;
-                acc.d0 += (long long)__popc(o.n0) - __popc(s0[i]);
-                acc.d1 += (long long)__popc(o.n1) - __popc(s1[i]);
+                set_acc_add(s_pc, x[i].s, (long long)__popc(o.n0) - __popc(s0[i]),
+                            (long long)__popc(o.n1) - __popc(s1[i]));
                 if (lanes_on) {
                     lane_deltas(s_lane, w0 + i, s0[i], o.n0);
                     if (P == 2) lane_deltas(s_lane + nl, w0 + i, s1[i], o.n1);
@@ -252,33 +262,37 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
         const bool leader = writer && tl == 0;
         const bool want = leader && fl != 0u;
         if (want && (fl & 1u)) acc.push_deg += (unsigned long long)(__ldg(A.out_ptr + v + 1) - __ldg(A.out_ptr + v));
-        if (A.prof_bytes && leader) acc.bytes += row_bytes(A, P, any_need != 0u, end - beg);
+        if (A.prof_bytes && leader) acc.bytes += row_bytes(SW, P, any_need != 0u, end - beg);
         list_append(A, want, (int32_t)((uint32_t)v | ((fl & 1u) ? kPushBit : 0u)), list_slot);
         if (sparse && leader) atomicAnd(&A.bitmap[v >> 5], ~(1u << (v & 31)));
     }
     flush_accum(A, acc, list_slot, WARP_ROW ? PK_MID : PK_SMALL);
+    set_acc_flush(A, s_pc);
     if (lanes_on) flush_lanes(A, s_lane, nl);
 }
 
-// Hub rows, phase 1: one CTA per chunk of in-arcs; per-lane partial counts (IC: live
-// masks) are added into the hub's scratch slot.
+// Hub rows, phase 1: one CTA per (chunk of in-arcs, word slice); per-lane partial counts
+// (IC: live masks) are added into the hub's scratch slot.
 template <int MODEL, int V, int TEAM>
 __global__ void __launch_bounds__(kBlock, min_ctas<V, true>()) k_hub_chunks(StepArgs A) {
     __shared__ uint32_t s_cnt[kMaxR];
     constexpr int B = kWideBits;
     constexpr int TPB = kBlock / TEAM;
+    constexpr int SW = TEAM * V;
     constexpr int P = ModelTraits<MODEL>::planes;
     const Ctl *C = A.ctl;
     if (*(volatile const int32_t *)&C->stop) return;
     const bool sparse = *(volatile const int32_t *)&C->sparse != 0;
-    const int nl = A.Ws * 32;
+    const int nl = A.Wn * 32;
     const int tl = threadIdx.x % TEAM;
     const int team = threadIdx.x / TEAM;
     const int lane = threadIdx.x & 31;
-    const int w0 = tl * V;
-    for (int i = threadIdx.x; i < nl; i += blockDim.x) s_cnt[i] = 0u;
+    for (int i = threadIdx.x; i < SW * 32; i += blockDim.x) s_cnt[i] = 0u;
     __syncthreads();
-    for (int64_t item = blockIdx.x; item < A.n_hub_chunks; item += gridDim.x) {
+    const int64_t n_items = A.n_hub_chunks * A.nslices;
+    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int64_t item = it / A.nslices;
+        const int slice = (int)(it - item * A.nslices);
         int lo = 0, hi = A.n_hubs - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -287,36 +301,41 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, true>()) k_hub_chunks(Step
         const int h = lo;
         const int32_t v = __ldg(A.hub_rows + h);
         if (sparse && !((A.bitmap[v >> 5] >> (v & 31)) & 1u)) continue;
+        const int ws0 = slice * SW;        // first word of the slice
+        const int w0 = ws0 + tl * V;
+        WordCtx x[V];
         uint32_t need[V];
         uint32_t any_need = 0u;
         {
-            const size_t off = (size_t)v * A.Ws + w0;
+            const size_t off = (size_t)v * A.Wn + w0;
             Vec<V> a = ldg_vec<V>(A.cur + off);
             Vec<V> b{};
             if (P == 2) b = ldg_vec<V>(A.cur + A.plane_words + off);
 #pragma unroll
             for (int i = 0; i < V; ++i) {
-                const uint32_t vm = word_valid_mask(A, w0 + i);
-                need[i] = MODEL == FSGP_SIR ? (vm & ~a.w[i] & ~b.w[i]) : (vm & ~a.w[i]);
+                x[i] = word_ctx(A, w0 + i);
+                need[i] = MODEL == FSGP_SIR ? (x[i].vm & ~a.w[i] & ~b.w[i]) : (x[i].vm & ~a.w[i]);
                 any_need |= need[i];
             }
         }
 #pragma unroll
         for (int o = 1; o < TEAM; o <<= 1) any_need |= __shfl_xor_sync(0xffffffffu, any_need, o);
-        if (!any_need) continue;   // identical in every team: the row is shared
+        if (!any_need) continue;   // identical in every team: they share the slice
         const int32_t rb = __ldg(A.row_ptr + v), re = __ldg(A.row_ptr + v + 1);
         const int64_t cidx = item - __ldg(A.hub_chunk_base + h);
         const int64_t beg = (int64_t)rb + cidx * A.hub_chunk;
         const int64_t end = min((int64_t)re, beg + A.hub_chunk);
         uint32_t c[V][B];
         uint32_t newly[V];
+        uint64_t ic_thr[V];
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             newly[i] = 0u;
+            ic_thr[i] = ModelTraits<MODEL>::counts ? 0ull : ic_threshold(A, x[i].s, re - rb);
 #pragma unroll
             for (int b = 0; b < B; ++b) c[i][b] = 0u;
         }
-        gather_arcs<MODEL, V, B>(A, beg + 4 * team, end, 4 * TPB, w0, need, ic_threshold(A, re - rb), c, newly);
+        gather_arcs<MODEL, V, B>(A, beg + 4 * team, end, 4 * TPB, w0, need, ic_thr, x, c, newly);
 #pragma unroll
         for (int o = TEAM; o < 32; o <<= 1) {
 #pragma unroll
@@ -334,36 +353,38 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, true>()) k_hub_chunks(Step
         if (lane < TEAM) {   // team 0 of the warp holds the warp's totals
 #pragma unroll
             for (int i = 0; i < V; ++i) {
-                const int w = w0 + i;
+                const int wsl = w0 + i - ws0;   // word within the slice
                 if constexpr (ModelTraits<MODEL>::counts) {
                     uint32_t nz = any_count<B>(c[i]);
                     while (nz) {
                         const int l = __ffs(nz) - 1;
                         nz &= nz - 1;
-                        uint32_t k = 0u;
-#pragma unroll
-                        for (int b = 0; b < B; ++b) k |= ((c[i][b] >> l) & 1u) << b;
-                        atomicAdd(&s_cnt[w * 32 + l], k);
+                        atomicAdd(&s_cnt[wsl * 32 + l], lane_count<B>(c[i], l));
                     }
                 } else {
-                    if (newly[i]) atomicOr(&s_cnt[w], newly[i]);
+                    if (newly[i]) atomicOr(&s_cnt[wsl], newly[i]);
                 }
             }
         }
-        if (A.prof_bytes && threadIdx.x == 0) {
-            const unsigned long long src = A.Ws * 4 > 32 ? (unsigned long long)A.Ws * 4ull : 32ull;
-            atomicAdd(&A.prof_bytes[PK_HUB], 8ull + (unsigned long long)P * 4ull * A.Ws +
-                                             (unsigned long long)(end - beg) * (4ull + src));
-        }
+        if (A.prof_bytes && threadIdx.x == 0)
+            atomicAdd(&A.prof_bytes[PK_HUB], row_bytes(SW, P, true, end - beg));
         __syncthreads();
         uint32_t *slot = A.hub_scratch + (size_t)h * nl;
-        const int lim = ModelTraits<MODEL>::counts ? nl : A.Ws;
-        for (int i = threadIdx.x; i < lim; i += blockDim.x) {
-            const uint32_t x = s_cnt[i];
-            if (x) {
-                if constexpr (ModelTraits<MODEL>::counts) atomicAdd(slot + i, x);
-                else atomicOr(slot + i, x);
-                s_cnt[i] = 0u;
+        if constexpr (ModelTraits<MODEL>::counts) {
+            for (int i = threadIdx.x; i < SW * 32; i += blockDim.x) {
+                const uint32_t xv = s_cnt[i];
+                if (xv) {
+                    atomicAdd(slot + ws0 * 32 + i, xv);
+                    s_cnt[i] = 0u;
+                }
+            }
+        } else {
+            for (int i = threadIdx.x; i < SW; i += blockDim.x) {
+                const uint32_t xv = s_cnt[i];
+                if (xv) {
+                    atomicOr(slot + ws0 + i, xv);
+                    s_cnt[i] = 0u;
+                }
             }
         }
         __syncthreads();
@@ -375,16 +396,16 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, true>()) k_hub_chunks(Step
 template <int MODEL>
 __global__ void __launch_bounds__(kBlock) k_hub_finalize(StepArgs A) {
     extern __shared__ int32_t s_lane[];
+    __shared__ unsigned long long s_pc[2 * kMaxSets];
     constexpr int P = ModelTraits<MODEL>::planes;
     const Ctl *C = A.ctl;
     if (*(volatile const int32_t *)&C->stop) return;
     const bool sparse = *(volatile const int32_t *)&C->sparse != 0;
-    const int nl = A.Ws * 32;
+    const int nl = A.Wn * 32;
     const bool lanes_on = A.lane_cnt != nullptr;
-    if (lanes_on) {
+    if (lanes_on)
         for (int i = threadIdx.x; i < 2 * nl; i += blockDim.x) s_lane[i] = 0;
-        __syncthreads();
-    }
+    set_acc_zero(s_pc, A.S);
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -397,15 +418,15 @@ __global__ void __launch_bounds__(kBlock) k_hub_finalize(StepArgs A) {
         if (cand) {
             const int32_t d = __ldg(A.row_ptr + v + 1) - __ldg(A.row_ptr + v);
             uint32_t *slot = A.hub_scratch + (size_t)h * nl;
-            for (int g0 = 0; g0 < A.Ws; g0 += 32) {
+            for (int g0 = 0; g0 < A.Wn; g0 += 32) {
                 const int w = g0 + lane;
-                const bool act = w < A.Ws;
+                const bool act = w < A.Wn;
                 uint32_t c[32];
 #pragma unroll
                 for (int b = 0; b < 32; ++b) c[b] = 0u;
                 uint32_t newly = 0u;
                 if constexpr (ModelTraits<MODEL>::counts) {
-                    const int nw = min(32, A.Ws - g0);
+                    const int nw = min(32, A.Wn - g0);
                     for (int ww = 0; ww < nw; ++ww) {
                         const uint32_t kv = slot[(g0 + ww) * 32 + lane];
                         if (kv) slot[(g0 + ww) * 32 + lane] = 0u;
@@ -422,25 +443,24 @@ __global__ void __launch_bounds__(kBlock) k_hub_finalize(StepArgs A) {
                     }
                 }
                 if (act) {
-                    const size_t off = (size_t)v * A.Ws + w;
+                    const size_t off = (size_t)v * A.Wn + w;
                     const uint32_t s0 = __ldg(A.cur + off);
                     const uint32_t s1 = P == 2 ? __ldg(A.cur + A.plane_words + off) : 0u;
-                    const uint32_t vm = word_valid_mask(A, w);
-                    const uint32_t g = A.gbase + (uint32_t)w;
+                    const WordCtx x = word_ctx(A, w);
                     WordOut o;
                     if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SIS) {
-                        o = update_sir_word<MODEL, 32>(A, (uint32_t)v, g, vm, s0, s1, c);
+                        o = update_sir_word<MODEL, 32>(A, (uint32_t)v, x, s0, s1, c);
                     } else if constexpr (MODEL == FSGP_IC) {
-                        const uint32_t nw2 = newly & vm & ~s0;
+                        const uint32_t nw2 = newly & x.vm & ~s0;
                         o.n0 = s0 | nw2;
                         o.n1 = nw2;
                     } else {
-                        o = update_lt_word<32>(A, (uint32_t)v, g, vm, s0, d, c);
+                        o = update_lt_word<32>(A, (uint32_t)v, x, s0, d, c);
                     }
                     A.nxt[off] = o.n0;
                     if (P == 2) A.nxt[A.plane_words + off] = o.n1;
-                    acc.d0 += (long long)__popc(o.n0) - __popc(s0);
-                    acc.d1 += (long long)__popc(o.n1) - __popc(s1);
+                    set_acc_add(s_pc, x.s, (long long)__popc(o.n0) - __popc(s0),
+                                (long long)__popc(o.n1) - __popc(s1));
                     if (lanes_on) {
                         lane_deltas(s_lane, w, s0, o.n0);
                         if (P == 2) lane_deltas(s_lane + nl, w, s1, o.n1);
@@ -455,11 +475,12 @@ __global__ void __launch_bounds__(kBlock) k_hub_finalize(StepArgs A) {
         const bool want = cand && lane == 0 && fl != 0u;
         if (want && (fl & 1u)) acc.push_deg += (unsigned long long)(__ldg(A.out_ptr + v + 1) - __ldg(A.out_ptr + v));
         if (A.prof_bytes && cand && lane == 0)
-            acc.bytes += row_bytes(A, P, false, 0) + 2ull * 4ull * 32ull * (unsigned long long)A.Ws;
+            acc.bytes += row_bytes(A.Wn, P, false, 0) + 2ull * 4ull * 32ull * (unsigned long long)A.Wn;
         list_append(A, want, (int32_t)((uint32_t)v | ((fl & 1u) ? kPushBit : 0u)), list_slot);
         if (sparse && cand && lane == 0) atomicAnd(&A.bitmap[v >> 5], ~(1u << (v & 31)));
     }
     flush_accum(A, acc, list_slot, PK_HUBFIN);
+    set_acc_flush(A, s_pc);
     if (lanes_on) flush_lanes(A, s_lane, nl);
 }
 

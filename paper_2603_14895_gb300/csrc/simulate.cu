@@ -3,6 +3,11 @@
 // Algorithm 1), the frontier path ("decide whether x needs to update", Algorithm 1),
 // and the reductions of the results (per-step compartment counts, per-node final
 // frequencies, per-realization counts; the 0/1/2 state conversion of Appendix A.1).
+//
+// Seed sets (and batched requests) with the same number of words per set run side by
+// side: set s owns words [s*Ws, (s+1)*Ws) of every node (Eq. batch, independent
+// randomness per realization; each set keeps its own key, so its result equals a run of
+// that set alone).
 #include <cuda_runtime.h>
 #include <limits.h>
 #include <math.h>
@@ -16,12 +21,20 @@
 
 namespace fsgp {
 
+// Device-side output pointers of one set.
+struct SetOut {
+    unsigned long long *counts;   // [T+1][3]
+    uint32_t *freq;               // [3][n]
+    uint32_t *per_real;           // [R][T+1][3]
+    uint32_t *planes;             // [P][n][W]
+};
+
 // ------------------------------------------------------------------------ kernels
 
-// Seed nodes: all valid lanes of the source planes set, in both buffers.
+// Seed nodes of one set: all valid lanes of its source planes, in both buffers.
 __global__ void k_seed(uint32_t *buf0, uint32_t *buf1, size_t plane_words, int both_planes,
-                       const int32_t *__restrict__ seeds, int64_t ns, int Ws, int W,
-                       uint32_t last_mask) {
+                       const int32_t *__restrict__ seeds, int64_t ns, int Wn, int ws0, int Ws,
+                       int W, uint32_t last_mask) {
     const int64_t total = ns * Ws;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -29,7 +42,7 @@ __global__ void k_seed(uint32_t *buf0, uint32_t *buf1, size_t plane_words, int b
         const int w = (int)(i % Ws);
         const int32_t v = seeds[si];
         const uint32_t m = w < W - 1 ? 0xffffffffu : (w == W - 1 ? last_mask : 0u);
-        const size_t off = (size_t)v * Ws + w;
+        const size_t off = (size_t)v * Wn + ws0 + w;
         buf0[off] = m;
         buf1[off] = m;
         if (both_planes) {
@@ -39,9 +52,9 @@ __global__ void k_seed(uint32_t *buf0, uint32_t *buf1, size_t plane_words, int b
     }
 }
 
-// Caller-supplied start planes [planes][n][W] -> both buffers [planes][n][Ws].
+// Caller-supplied start planes of one set [planes][n][W] -> both buffers.
 __global__ void k_import(const uint32_t *__restrict__ in, int planes, int32_t n, int W, int Ws,
-                         uint32_t last_mask, uint32_t *buf0, uint32_t *buf1) {
+                         int Wn, int ws0, uint32_t last_mask, uint32_t *buf0, uint32_t *buf1) {
     const int64_t total = (int64_t)planes * n * Ws;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -52,20 +65,21 @@ __global__ void k_import(const uint32_t *__restrict__ in, int planes, int32_t n,
             x = in[pv * W + w];
             if (w == W - 1) x &= last_mask;
         }
-        buf0[i] = x;
-        buf1[i] = x;
+        const size_t o = (size_t)pv * Wn + ws0 + w;
+        buf0[o] = x;
+        buf1[o] = x;
     }
 }
 
-// Step-0 totals, per-lane counts and the rows whose source lanes push at step 1.
+// Step-0 totals per set, per-lane counts and the rows whose source lanes push at step 1.
 __global__ void __launch_bounds__(kBlock) k_init_scan(StepArgs A, int model) {
     extern __shared__ int32_t s_lane[];
-    const int nl = A.Ws * 32;
+    __shared__ unsigned long long s_pc[2 * kMaxSets];
+    const int nl = A.Wn * 32;
     const bool lanes_on = A.lane_cnt != nullptr;
-    if (lanes_on) {
+    if (lanes_on)
         for (int i = threadIdx.x; i < 2 * nl; i += blockDim.x) s_lane[i] = 0;
-        __syncthreads();
-    }
+    set_acc_zero(s_pc, A.S);
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -76,12 +90,11 @@ __global__ void __launch_bounds__(kBlock) k_init_scan(StepArgs A, int model) {
         const bool has = v < A.n;
         bool push = false;
         if (has) {
-            for (int w = 0; w < A.Ws; ++w) {
-                const size_t off = (size_t)v * A.Ws + w;
+            for (int w = 0; w < A.Wn; ++w) {
+                const size_t off = (size_t)v * A.Wn + w;
                 const uint32_t s0 = A.cur[off];
                 const uint32_t s1 = two ? A.cur[A.plane_words + off] : 0u;
-                acc.d0 += __popc(s0);
-                acc.d1 += __popc(s1);
+                set_acc_add(s_pc, w >> A.ws_shift, __popc(s0), __popc(s1));
                 if (lanes_on) {
                     lane_deltas(s_lane, w, 0u, s0);
                     if (two) lane_deltas(s_lane + nl, w, 0u, s1);
@@ -90,10 +103,11 @@ __global__ void __launch_bounds__(kBlock) k_init_scan(StepArgs A, int model) {
             }
         }
         if (push) acc.push_deg += (unsigned long long)(A.out_ptr[v + 1] - A.out_ptr[v]);
-        if (has && A.prof_bytes) acc.bytes += (two ? 2ull : 1ull) * 4ull * (unsigned long long)A.Ws;
+        if (has && A.prof_bytes) acc.bytes += (two ? 2ull : 1ull) * 4ull * (unsigned long long)A.Wn;
         list_append(A, has && push, (int32_t)((uint32_t)v | kPushBit), 0);
     }
     flush_accum(A, acc, 0, PK_INIT);
+    set_acc_flush(A, s_pc);
     if (lanes_on) flush_lanes(A, s_lane, nl);
 }
 
@@ -108,32 +122,39 @@ __device__ __forceinline__ void compartments(int model, int64_t total, int64_t p
     }
 }
 
-// Per-realization snapshot of the running lane counts into per_real[r][kk][3].
-__device__ void snapshot_lanes(const StepArgs &A, int model, uint32_t *per_real, int R, int T1,
-                               int kk) {
-    const int nl = A.Ws * 32;
-    for (int r = threadIdx.x + blockIdx.x * blockDim.x; r < R; r += blockDim.x * gridDim.x) {
+// Per-realization snapshot of the running lane counts into per_real[r][kk][3] of every
+// set that asked for it.
+__device__ void snapshot_lanes(const StepArgs &A, int model, const SetOut *outs, int T1, int kk) {
+    const int nl = A.Wn * 32;
+    const int per_set = A.Ws * 32;
+    for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < nl; i += blockDim.x * gridDim.x) {
+        const int s = i / per_set, r = i - s * per_set;
+        uint32_t *pr = outs[s].per_real;
+        if (!pr || r >= A.sp[s].R) continue;
         int64_t o[3];
-        compartments(model, A.n, A.lane_cnt[r], A.lane_cnt[nl + r], o);
-        uint32_t *dst = per_real + ((size_t)r * T1 + kk) * 3;
+        compartments(model, A.n, A.lane_cnt[i], A.lane_cnt[nl + i], o);
+        uint32_t *dst = pr + ((size_t)r * T1 + kk) * 3;
         dst[0] = (uint32_t)o[0];
         dst[1] = (uint32_t)o[1];
         dst[2] = (uint32_t)o[2];
     }
 }
 
-// Start of step k: quiescence test (IC/LT), running totals, dense/sparse choice, and the
-// per-realization snapshot of step k-1.
+// Start of step k: quiescence test (IC/LT, all sets), running totals, dense/sparse
+// choice, and the per-realization snapshot of step k-1.
 __global__ void k_begin(StepArgs A, int model, unsigned long long sparse_limit, int force_dense,
-                        uint32_t *per_real, int R, int T1) {
-    if (per_real) snapshot_lanes(A, model, per_real, R, T1, A.k - 1);
+                        const SetOut *outs, int T1) {
+    if (A.lane_cnt) snapshot_lanes(A, model, outs, T1, A.k - 1);
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     Ctl *C = A.ctl;
-    unsigned long long *prev = A.pc - 2;
-    A.pc[0] = prev[0];
-    A.pc[1] = prev[1];
+    const unsigned long long *prev = A.pc - 2 * A.S;
+    bool quiet = true;
+    for (int i = 0; i < 2 * A.S; ++i) {
+        A.pc[i] = prev[i];
+        if ((i & 1) && prev[i]) quiet = false;
+    }
     if (C->stop) return;
-    if ((model == FSGP_IC || model == FSGP_LT) && prev[1] == 0ull) {
+    if ((model == FSGP_IC || model == FSGP_LT) && quiet) {
         C->stop = 1;
         return;
     }
@@ -198,52 +219,61 @@ __global__ void __launch_bounds__(kBlock) k_mark(StepArgs A) {
     }
 }
 
-// Results: compartment totals per step, steps run, last per-realization snapshot.
-__global__ void k_finalize(StepArgs A, int model, int T, unsigned long long NR,
-                           const unsigned long long *pc_all, unsigned long long *counts,
-                           int32_t *steps_run, uint32_t *per_real, int R) {
-    for (int k = threadIdx.x + blockIdx.x * blockDim.x; k <= T; k += blockDim.x * gridDim.x) {
+// Results per set: compartment totals per step and the last per-realization snapshot.
+__global__ void k_finalize(StepArgs A, int model, int T, const unsigned long long *pc_all,
+                           const SetOut *outs) {
+    const int S = A.S;
+    for (int64_t i = threadIdx.x + (int64_t)blockIdx.x * blockDim.x; i < (int64_t)(T + 1) * S;
+         i += (int64_t)blockDim.x * gridDim.x) {
+        const int k = (int)(i / S), s = (int)(i % S);
         int64_t o[3];
-        compartments(model, (int64_t)NR, (int64_t)pc_all[2 * k], (int64_t)pc_all[2 * k + 1], o);
-        counts[3 * k] = (unsigned long long)o[0];
-        counts[3 * k + 1] = (unsigned long long)o[1];
-        counts[3 * k + 2] = (unsigned long long)o[2];
+        const int64_t NR = (int64_t)A.n * A.sp[s].R;
+        const unsigned long long *p = pc_all + ((size_t)k * S + s) * 2;
+        compartments(model, NR, (int64_t)p[0], (int64_t)p[1], o);
+        unsigned long long *c = outs[s].counts + 3 * (size_t)k;
+        c[0] = (unsigned long long)o[0];
+        c[1] = (unsigned long long)o[1];
+        c[2] = (unsigned long long)o[2];
     }
-    if (per_real) snapshot_lanes(A, model, per_real, R, T + 1, T);
-    if (steps_run && blockIdx.x == 0 && threadIdx.x == 0) *steps_run = A.ctl->steps_done;
+    if (A.lane_cnt) snapshot_lanes(A, model, outs, T + 1, T);
 }
 
-// Per-node final compartment frequencies.
-__global__ void k_freq(StepArgs A, int model, const uint32_t *buf0, const uint32_t *buf1, int R,
-                       uint32_t *freq) {
+// Per-node final compartment frequencies of every set that asked for them.
+__global__ void k_freq(StepArgs A, int model, const uint32_t *buf0, const uint32_t *buf1,
+                       const SetOut *outs) {
     const uint32_t *st = (A.ctl->steps_done & 1) ? buf1 : buf0;
     const bool two = model != FSGP_SIS;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < A.n;
          v += (int64_t)gridDim.x * blockDim.x) {
-        int64_t p0 = 0, p1 = 0;
-        for (int w = 0; w < A.W; ++w) {
-            const size_t off = (size_t)v * A.Ws + w;
-            p0 += __popc(st[off]);
-            if (two) p1 += __popc(st[A.plane_words + off]);
+        for (int s = 0; s < A.S; ++s) {
+            uint32_t *fr = outs[s].freq;
+            if (!fr) continue;
+            const int W = A.sp[s].W;
+            int64_t p0 = 0, p1 = 0;
+            for (int w = 0; w < W; ++w) {
+                const size_t off = (size_t)v * A.Wn + (size_t)s * A.Ws + w;
+                p0 += __popc(st[off]);
+                if (two) p1 += __popc(st[A.plane_words + off]);
+            }
+            int64_t o[3];
+            compartments(model, A.sp[s].R, p0, p1, o);
+            fr[v] = (uint32_t)o[0];
+            fr[(size_t)A.n + v] = (uint32_t)o[1];
+            fr[2 * (size_t)A.n + v] = (uint32_t)o[2];
         }
-        int64_t o[3];
-        compartments(model, R, p0, p1, o);
-        freq[v] = (uint32_t)o[0];
-        freq[(size_t)A.n + v] = (uint32_t)o[1];
-        freq[2 * (size_t)A.n + v] = (uint32_t)o[2];
     }
 }
 
-// Final planes -> caller layout [planes][n][W].
-__global__ void k_export(StepArgs A, int planes, const uint32_t *buf0, const uint32_t *buf1,
-                         uint32_t *out) {
+// Final planes of one set -> caller layout [planes][n][W].
+__global__ void k_export(StepArgs A, int planes, int ws0, int W, const uint32_t *buf0,
+                         const uint32_t *buf1, uint32_t *out) {
     const uint32_t *st = (A.ctl->steps_done & 1) ? buf1 : buf0;
-    const int64_t total = (int64_t)planes * A.n * A.W;
+    const int64_t total = (int64_t)planes * A.n * W;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int w = (int)(i % A.W);
-        const int64_t pv = i / A.W;
-        out[i] = st[(size_t)pv * A.Ws + w];
+        const int w = (int)(i % W);
+        const int64_t pv = i / W;
+        out[i] = st[(size_t)pv * A.Wn + ws0 + w];
     }
 }
 
@@ -309,11 +339,6 @@ static int ensure_hub_table(fsgp_graph *g, int hub_min_deg, int chunk, cudaStrea
     return FSGP_OK;
 }
 
-struct WsLayout {
-    size_t off[16];
-    size_t total;
-};
-
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static int ensure_workspace(fsgp_graph *g, size_t bytes) {
@@ -345,74 +370,53 @@ static int occupancy_model(int model, int V, int TEAM, size_t smem, int *a, int 
     }
 }
 
-}  // namespace fsgp
-
-using namespace fsgp;
-
-extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_params *params,
-                             const int32_t *seed_nodes, const int64_t *seed_offsets,
-                             int32_t n_sets, uint32_t seed_flags, int32_t R, int32_t T,
-                             uint64_t rng_seed, const fsgp_options *opt_in, fsgp_result *out,
-                             void *stream) {
-    set_error("");
-    fsgp_graph *g = const_cast<fsgp_graph *>(gc);
-    if (!g) return fail(FSGP_EINVAL, "graph is NULL");
-    if (model < FSGP_SIR || model > FSGP_LT) return fail(FSGP_EINVAL, "unknown model");
-    if (!params) return fail(FSGP_EINVAL, "params is NULL");
-    if (!out || !out->counts) return fail(FSGP_EINVAL, "result counts buffer is NULL");
-    if (out->flags != FSGP_PTR_HOST && out->flags != FSGP_PTR_DEVICE)
-        return fail(FSGP_EINVAL, "bad result flags");
-    if (R < 1 || R > kMaxR) return fail(FSGP_EINVAL, "R must be in [1, 4096]");
-    if (T < 0) return fail(FSGP_EINVAL, "T must be >= 0");
-    if (n_sets < 1) return fail(FSGP_EINVAL, "n_sets must be >= 1");
-    auto bad_p = [](double p) { return !(p >= 0.0 && p <= 1.0); };
-    if (bad_p(params->beta) || bad_p(params->gamma) || bad_p(params->ic_p))
-        return fail(FSGP_EINVAL, "probabilities must lie in [0, 1]");
-    if (params->ic_mode != FSGP_IC_WEIGHTED_CASCADE && params->ic_mode != FSGP_IC_CONSTANT)
-        return fail(FSGP_EINVAL, "bad ic_mode");
-    fsgp_options opt{};
-    if (opt_in) opt = *opt_in;
-    if (opt.r_offset < 0 || (opt.r_offset & 31)) return fail(FSGP_EINVAL, "r_offset must be a non-negative multiple of 32");
-    if (opt.t0 < 0) return fail(FSGP_EINVAL, "t0 must be >= 0");
-    if ((int64_t)opt.t0 + T > (int64_t)UINT32_MAX) return fail(FSGP_EINVAL, "t0 + T too large");
-    const bool use_init = opt.init_planes != nullptr;
-    if (!use_init) {
-        if (!seed_offsets) return fail(FSGP_EINVAL, "seed_offsets is NULL");
-        if (seed_flags != FSGP_PTR_HOST && seed_flags != FSGP_PTR_DEVICE) return fail(FSGP_EINVAL, "bad seed flags");
-        if (seed_offsets[0] != 0) return fail(FSGP_EINVAL, "seed_offsets[0] must be 0");
-        for (int s = 0; s < n_sets; ++s)
-            if (seed_offsets[s + 1] < seed_offsets[s]) return fail(FSGP_EINVAL, "seed_offsets must be non-decreasing");
-        if (seed_offsets[n_sets] > 0 && !seed_nodes) return fail(FSGP_EINVAL, "seed_nodes is NULL");
-        const int64_t ns_all = seed_offsets[n_sets];
-        std::vector<int32_t> host_copy;
-        const int32_t *hs = seed_nodes;
-        if (seed_flags == FSGP_PTR_DEVICE && ns_all > 0) {
-            host_copy.resize((size_t)ns_all);
-            FSGP_CUDA(cudaMemcpy(host_copy.data(), seed_nodes, sizeof(int32_t) * (size_t)ns_all,
-                                 cudaMemcpyDeviceToHost));
-            hs = host_copy.data();
-        }
-        for (int64_t i = 0; i < ns_all; ++i)
-            if (hs[i] < 0 || hs[i] >= g->n) return fail(FSGP_EINVAL, "seed node out of range");
-    }
-    int dev = 0;
-    FSGP_CUDA(cudaGetDevice(&dev));
-    if (dev != g->device) return fail(FSGP_EINVAL, "current device differs from the graph's device");
-    cudaStream_t s = (cudaStream_t)stream;
-
-    // ---------------------------------------------------------------- shape
-    const int32_t n = g->n;
+static int words_per_set(int R) {
     const int W = (R + 31) / 32;
     int Ws = 1;
     while (Ws < W) Ws <<= 1;
+    return Ws;
+}
+
+// Survival table for one beta, up to min(K_sat, max in-degree); ksat = INT32_MAX if the
+// table never reaches zero.
+static void survival_table(double beta, int32_t max_deg, std::vector<uint64_t> &out, int32_t *ksat) {
+    const uint64_t b = (uint64_t)llrint(beta * 4294967296.0);
+    const uint64_t q = TWO32 - b;
+    out.push_back(TWO32);
+    *ksat = INT32_MAX;
+    uint64_t prev = TWO32;
+    for (int64_t k = 1; k <= max_deg; ++k) {
+        const uint64_t cur = (q == TWO32) ? prev : (prev * q) >> 32;
+        out.push_back(cur);
+        prev = cur;
+        if (cur == 0) {
+            *ksat = (int32_t)k;
+            break;
+        }
+    }
+}
+
+// One launch sequence over S sets that share Ws.
+static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const *sets, int S,
+                    int Ws, int T, const fsgp_options &opt, cudaStream_t s) {
+    const int32_t n = g->n;
     const int P = fsgp_model_planes(model);
-    const uint32_t last_mask = (R & 31) ? ((1u << (R & 31)) - 1u) : 0xffffffffu;
-    int V = opt.vector_words ? opt.vector_words : std::min(2, Ws);   // measured best on GB300
-    if (!opt.vector_words && Ws / V > 32) V = Ws / 32;                // R > 2048: 4 words/thread
+    const int Wn = S * Ws;
+    const int pd = Ws << __builtin_ctz((unsigned)S);   // largest power of two dividing Wn
+    int V = opt.vector_words ? opt.vector_words : 2;   // 2 measured best on GB300
     if (V != 1 && V != 2 && V != 4) return fail(FSGP_EINVAL, "vector_words must be 1, 2 or 4");
-    if (V > Ws) V = Ws;
-    const int TEAM = Ws / V;
-    if (TEAM > 32) return fail(FSGP_EINVAL, "vector_words too small for R");
+    if (V > pd) V = pd;
+    const int SW = std::min(32 * V, pd);
+    const int TEAM = SW / V;
+    const int nslices = Wn / SW;
+    const bool host_out = sets[0]->out_flags == FSGP_PTR_HOST;
+    bool want_lanes = false, want_freq = false, any_init = false, want_steps = false;
+    for (int i = 0; i < S; ++i) {
+        want_lanes |= sets[i]->per_real != nullptr;
+        want_freq |= sets[i]->freq != nullptr;
+        any_init |= sets[i]->init_planes != nullptr;
+        want_steps |= sets[i]->steps_run != nullptr;
+    }
     // degree classes
     int small_max = opt.small_max_deg > 0 ? opt.small_max_deg : 255;
     int hub_min = opt.hub_min_deg > 0 ? opt.hub_min_deg : 8192;
@@ -439,49 +443,58 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
     const int32_t n_mid = start_small - start_mid;
     const int32_t n_small = n - start_small;
 
-    // -------------------------------------------------------- survival table
-    std::vector<uint64_t> surv;
-    int32_t ksat = INT32_MAX;
-    if (model == FSGP_SIR || model == FSGP_SIS) {
-        const uint64_t b = (uint64_t)llrint(params->beta * 4294967296.0);
-        const uint64_t q = TWO32 - b;
-        surv.push_back(TWO32);
-        for (int64_t k = 1; k <= g->max_deg; ++k) {
-            const uint64_t prev = surv.back();
-            const uint64_t cur = (q == TWO32) ? prev : (prev * q) >> 32;
-            surv.push_back(cur);
-            if (cur == 0) {
-                ksat = (int32_t)k;
-                break;
-            }
-        }
-    } else {
-        surv.push_back(TWO32);
+    // per-set parameters and survival tables
+    std::vector<uint64_t> surv_all;
+    std::vector<size_t> surv_off((size_t)S);
+    std::vector<SetParams> hp((size_t)S);
+    int64_t seeds_total = 0, preal_total = 0, planes_total = 0;
+    std::vector<int64_t> seed_off((size_t)S), preal_off((size_t)S), planes_off((size_t)S);
+    for (int i = 0; i < S; ++i) {
+        const SetSpec &x = *sets[i];
+        SetParams &p = hp[i];
+        surv_off[i] = surv_all.size();
+        int32_t ksat = INT32_MAX;
+        if (model == FSGP_SIR || model == FSGP_SIS) survival_table(x.beta, g->max_deg, surv_all, &ksat);
+        else surv_all.push_back(TWO32);
+        p.key0 = (uint32_t)(x.rng_seed & 0xffffffffu);
+        p.key1 = (uint32_t)(x.rng_seed >> 32);
+        p.ksat = ksat;
+        p.W = (x.R + 31) / 32;
+        p.last_mask = (x.R & 31) ? ((1u << (x.R & 31)) - 1u) : 0xffffffffu;
+        p.R = x.R;
+        p.g_rec = (uint64_t)llrint(x.gamma * 4294967296.0);
+        p.p_const = (uint64_t)llrint(x.ic_p * 4294967296.0);
+        seed_off[i] = seeds_total;
+        if (!x.init_planes && x.seed_flags == FSGP_PTR_HOST) seeds_total += x.n_seeds;
+        preal_off[i] = preal_total;
+        if (x.per_real) preal_total += (int64_t)x.R * (T + 1) * 3;
+        planes_off[i] = planes_total;
+        if (x.final_planes || x.init_planes) planes_total += (int64_t)P * n * p.W;
     }
 
     // ---------------------------------------------------------------- workspace
-    const bool want_lanes = out->per_real != nullptr;
-    const bool host_out = out->flags == FSGP_PTR_HOST;
-    const size_t state_words = (size_t)P * n * Ws;
-    const int64_t total_seeds = use_init ? 0 : seed_offsets[n_sets];
+    const size_t T1 = (size_t)T + 1;
+    const size_t state_words = (size_t)P * n * Wn;
     enum { O_STATE, O_PC, O_CTL, O_LIST0, O_LIST1, O_CSMALL, O_CMID, O_BITMAP, O_LANES,
-           O_HUB, O_SURV, O_SEEDS, O_COUNTS, O_FREQ, O_PREAL, O_PLANES, O_PROF, O_END };
+           O_HUB, O_SURV, O_SEEDS, O_COUNTS, O_FREQ, O_PREAL, O_PLANES, O_PROF, O_SP, O_OUT, O_END };
     size_t sz[O_END] = {0};
     sz[O_STATE] = 2 * state_words * sizeof(uint32_t);
-    sz[O_PC] = (size_t)(T + 1) * 2 * sizeof(unsigned long long);
+    sz[O_PC] = T1 * S * 2 * sizeof(unsigned long long);
     sz[O_CTL] = sizeof(Ctl);
-    sz[O_LIST0] = sz[O_LIST1] = (size_t)n * sizeof(int32_t);
+    sz[O_LIST0] = sz[O_LIST1] = (size_t)n * nslices * sizeof(int32_t);
     sz[O_CSMALL] = sz[O_CMID] = (size_t)n * sizeof(int32_t);
     sz[O_BITMAP] = ((size_t)n + 31) / 32 * sizeof(uint32_t);
-    sz[O_LANES] = want_lanes ? 2 * (size_t)Ws * 32 * sizeof(int32_t) : 0;
-    sz[O_HUB] = (size_t)n_hubs * Ws * 32 * sizeof(uint32_t);
-    sz[O_SURV] = surv.size() * sizeof(uint64_t);
-    sz[O_SEEDS] = (!use_init && seed_flags == FSGP_PTR_HOST) ? (size_t)total_seeds * sizeof(int32_t) : 0;
-    sz[O_COUNTS] = host_out ? (size_t)(T + 1) * 3 * sizeof(uint64_t) : 0;
-    sz[O_FREQ] = (host_out && out->freq) ? 3 * (size_t)n * sizeof(uint32_t) : 0;
-    sz[O_PREAL] = (host_out && out->per_real) ? (size_t)R * (T + 1) * 3 * sizeof(uint32_t) : 0;
-    sz[O_PLANES] = ((host_out && out->final_planes) || use_init) ? (size_t)P * n * W * sizeof(uint32_t) : 0;
+    sz[O_LANES] = want_lanes ? 2 * (size_t)Wn * 32 * sizeof(int32_t) : 0;
+    sz[O_HUB] = (size_t)n_hubs * Wn * 32 * sizeof(uint32_t);
+    sz[O_SURV] = surv_all.size() * sizeof(uint64_t);
+    sz[O_SEEDS] = (size_t)seeds_total * sizeof(int32_t);
+    sz[O_COUNTS] = host_out ? T1 * 3 * S * sizeof(uint64_t) : 0;
+    sz[O_FREQ] = (host_out && want_freq) ? 3 * (size_t)n * S * sizeof(uint32_t) : 0;
+    sz[O_PREAL] = host_out ? (size_t)preal_total * sizeof(uint32_t) : 0;
+    sz[O_PLANES] = (host_out || any_init) ? (size_t)planes_total * sizeof(uint32_t) : 0;
     sz[O_PROF] = FSGP_PROF_KINDS * sizeof(unsigned long long);
+    sz[O_SP] = (size_t)S * sizeof(SetParams);
+    sz[O_OUT] = (size_t)S * sizeof(SetOut);
     size_t off[O_END], total = 0;
     for (int i = 0; i < O_END; ++i) {
         off[i] = total;
@@ -495,27 +508,42 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
     unsigned long long *pc = (unsigned long long *)(ws + off[O_PC]);
     Ctl *ctl = (Ctl *)(ws + off[O_CTL]);
     int32_t *list[2] = {(int32_t *)(ws + off[O_LIST0]), (int32_t *)(ws + off[O_LIST1])};
-    int32_t *cand_small = (int32_t *)(ws + off[O_CSMALL]);
-    int32_t *cand_mid = (int32_t *)(ws + off[O_CMID]);
-    uint32_t *bitmap = (uint32_t *)(ws + off[O_BITMAP]);
-    int32_t *lanes = want_lanes ? (int32_t *)(ws + off[O_LANES]) : nullptr;
     uint32_t *hub_scratch = (uint32_t *)(ws + off[O_HUB]);
     uint64_t *d_surv = (uint64_t *)(ws + off[O_SURV]);
     unsigned long long *d_prof = (unsigned long long *)(ws + off[O_PROF]);
-    Prof prof;
-    const bool profiling = opt.profile != nullptr;
-    int64_t launches = 0;   // kernels launched by this call (profile only)
-    FSGP_CUDA(cudaMemcpyAsync(d_surv, surv.data(), sz[O_SURV], cudaMemcpyHostToDevice, s));
+    SetParams *d_sp = (SetParams *)(ws + off[O_SP]);
+    SetOut *d_out = (SetOut *)(ws + off[O_OUT]);
+    for (int i = 0; i < S; ++i) hp[i].surv = d_surv + surv_off[i];
+    FSGP_CUDA(cudaMemcpyAsync(d_surv, surv_all.data(), sz[O_SURV], cudaMemcpyHostToDevice, s));
+    FSGP_CUDA(cudaMemcpyAsync(d_sp, hp.data(), sz[O_SP], cudaMemcpyHostToDevice, s));
+    // device output pointers of each set (caller memory, or staging for host results)
+    std::vector<SetOut> ho((size_t)S);
+    for (int i = 0; i < S; ++i) {
+        const SetSpec &x = *sets[i];
+        SetOut &o = ho[i];
+        if (host_out) {
+            o.counts = (unsigned long long *)(ws + off[O_COUNTS]) + (size_t)i * T1 * 3;
+            o.freq = x.freq ? (uint32_t *)(ws + off[O_FREQ]) + (size_t)i * 3 * n : nullptr;
+            o.per_real = x.per_real ? (uint32_t *)(ws + off[O_PREAL]) + preal_off[i] : nullptr;
+            o.planes = x.final_planes ? (uint32_t *)(ws + off[O_PLANES]) + planes_off[i] : nullptr;
+        } else {
+            o.counts = (unsigned long long *)x.counts;
+            o.freq = x.freq;
+            o.per_real = x.per_real;
+            o.planes = x.final_planes;
+        }
+    }
+    FSGP_CUDA(cudaMemcpyAsync(d_out, ho.data(), sz[O_OUT], cudaMemcpyHostToDevice, s));
 
     // ---------------------------------------------------------------- launch shape
-    const size_t smem_lanes = want_lanes ? 2 * (size_t)Ws * 32 * sizeof(int32_t) : 0;
-    if (smem_lanes > 48 * 1024) {
-        // 2 planes x 4096 lanes x 4 B = 32 KB at most: always below the default limit
-        return fail(FSGP_EINVAL, "per-lane counters exceed shared memory");
-    }
+    const size_t smem_lanes = want_lanes ? 2 * (size_t)Wn * 32 * sizeof(int32_t) : 0;
+    if (smem_lanes > 32 * 1024) return fail(FSGP_EINVAL, "per-lane counters exceed shared memory");
     int bps_rows = 1, bps_hub = 1;
     rc = occupancy_model(model, V, TEAM, smem_lanes, &bps_rows, &bps_hub);
     if (rc) return rc;
+    Prof prof;
+    const bool profiling = opt.profile != nullptr;
+    int64_t launches = 0;
     StepLaunch L{};
     L.V = V;
     L.TEAM = TEAM;
@@ -524,12 +552,14 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
     L.have_mid = n_mid > 0;
     L.have_hub = n_hubs > 0;
     L.prof = profiling ? &prof : nullptr;
-    const int rows_per_block_small = (kBlock / 32) * (32 / TEAM);
+    const int64_t items_small = (int64_t)n_small * nslices, items_mid = (int64_t)n_mid * nslices;
+    const int per_block_small = (kBlock / 32) * (32 / TEAM);
     L.grid_small = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * bps_rows,
-                                                               ((int64_t)n_small + rows_per_block_small - 1) / rows_per_block_small));
+                                                               (items_small + per_block_small - 1) / per_block_small));
     L.grid_mid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * bps_rows,
-                                                             ((int64_t)n_mid + (kBlock / 32) - 1) / (kBlock / 32)));
-    L.grid_hub = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * bps_hub, g->hub.n_chunks));
+                                                             (items_mid + (kBlock / 32) - 1) / (kBlock / 32)));
+    L.grid_hub = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * bps_hub,
+                                                             g->hub.n_chunks * nslices));
     L.grid_fin = (int)std::max<int64_t>(1, ((int64_t)n_hubs + (kBlock / 32) - 1) / (kBlock / 32));
     const int grid_mark = g->sm_count * 8;
     const int grid_scan = grid_cap((int64_t)n, kBlock, g->sm_count, 8);
@@ -541,29 +571,25 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
     A.out_dst = g->out_dst;
     A.n = n;
     A.Ws = Ws;
-    A.W = W;
-    A.last_mask = last_mask;
+    A.ws_shift = __builtin_ctz((unsigned)Ws);
+    A.S = S;
+    A.Wn = Wn;
+    A.nslices = nslices;
     A.gbase = (uint32_t)(opt.r_offset >> 5);
     A.small_max_deg = small_max;
     A.hub_min_deg = hub_min;
-    A.plane_words = (size_t)n * Ws;
-    A.surv = d_surv;
-    A.surv_last = (int32_t)surv.size() - 1;
-    A.ksat = ksat;
-    A.g_rec = (uint64_t)llrint(params->gamma * 4294967296.0);
-    A.p_const = (uint64_t)llrint(params->ic_p * 4294967296.0);
-    A.ic_mode = params->ic_mode;
-    A.key0 = (uint32_t)(rng_seed & 0xffffffffu);
-    A.key1 = (uint32_t)(rng_seed >> 32);
+    A.plane_words = (size_t)n * Wn;
+    A.sp = d_sp;
+    A.ic_mode = ic_mode;
     A.ctl = ctl;
-    A.lane_cnt = lanes;
+    A.lane_cnt = want_lanes ? (int32_t *)(ws + off[O_LANES]) : nullptr;
     A.rows_small = g->rows_sorted + start_small;
     A.rows_mid = g->rows_sorted + start_mid;
     A.n_small = n_small;
     A.n_mid = n_mid;
-    A.cand_small = cand_small;
-    A.cand_mid = cand_mid;
-    A.bitmap = bitmap;
+    A.cand_small = (int32_t *)(ws + off[O_CSMALL]);
+    A.cand_mid = (int32_t *)(ws + off[O_CMID]);
+    A.bitmap = (uint32_t *)(ws + off[O_BITMAP]);
     A.hub_rows = g->hub.d_rows;
     A.hub_chunk_base = g->hub.d_chunk_base;
     A.n_hubs = n_hubs;
@@ -572,149 +598,284 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
     A.hub_scratch = hub_scratch;
     A.prof_bytes = profiling ? d_prof : nullptr;
 
-    const size_t T1 = (size_t)T + 1;
-    for (int set = 0; set < n_sets; ++set) {
-        // outputs of this set (device pointers: caller's or staging)
-        unsigned long long *counts_d = host_out ? (unsigned long long *)(ws + off[O_COUNTS])
-                                                : (unsigned long long *)(out->counts + (size_t)set * T1 * 3);
-        uint32_t *freq_d = !out->freq ? nullptr
-                           : host_out ? (uint32_t *)(ws + off[O_FREQ]) : out->freq + (size_t)set * 3 * n;
-        uint32_t *preal_d = !out->per_real ? nullptr
-                            : host_out ? (uint32_t *)(ws + off[O_PREAL]) : out->per_real + (size_t)set * R * T1 * 3;
-        uint32_t *planes_d = !out->final_planes ? nullptr
-                             : host_out ? (uint32_t *)(ws + off[O_PLANES]) : out->final_planes + (size_t)set * P * n * W;
-        int32_t *steps_d = (out->steps_run && !host_out) ? out->steps_run + set : nullptr;
-
-        FSGP_CUDA(cudaMemsetAsync(ws + off[O_STATE], 0, sz[O_STATE], s));
-        FSGP_CUDA(cudaMemsetAsync(pc, 0, sz[O_PC], s));
-        FSGP_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
-        {
-            // the step-0 scan always lists the pushing rows for step 1
-            const int32_t one[3] = {1, 1, 0};
-            FSGP_CUDA(cudaMemcpyAsync(&ctl->build_list, one, sizeof one, cudaMemcpyHostToDevice, s));
-        }
-        FSGP_CUDA(cudaMemsetAsync(bitmap, 0, sz[O_BITMAP], s));
-        if (lanes) FSGP_CUDA(cudaMemsetAsync(lanes, 0, sz[O_LANES], s));
-        if (sz[O_HUB]) FSGP_CUDA(cudaMemsetAsync(hub_scratch, 0, sz[O_HUB], s));
-        if (profiling) {
-            FSGP_CUDA(cudaMemsetAsync(d_prof, 0, sz[O_PROF], s));
-            prof.start(PK_INIT, s);
-        }
-
-        if (use_init) {
-            const uint32_t *src = opt.init_planes + (size_t)set * P * n * W;
+    FSGP_CUDA(cudaMemsetAsync(ws + off[O_STATE], 0, sz[O_STATE], s));
+    FSGP_CUDA(cudaMemsetAsync(pc, 0, sz[O_PC], s));
+    FSGP_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+    {
+        // the step-0 scan always lists the pushing rows for step 1
+        static const int32_t one[3] = {1, 1, 0};
+        FSGP_CUDA(cudaMemcpyAsync(&ctl->build_list, one, sizeof one, cudaMemcpyHostToDevice, s));
+    }
+    FSGP_CUDA(cudaMemsetAsync(A.bitmap, 0, sz[O_BITMAP], s));
+    if (A.lane_cnt) FSGP_CUDA(cudaMemsetAsync(A.lane_cnt, 0, sz[O_LANES], s));
+    if (sz[O_HUB]) FSGP_CUDA(cudaMemsetAsync(hub_scratch, 0, sz[O_HUB], s));
+    if (profiling) {
+        FSGP_CUDA(cudaMemsetAsync(d_prof, 0, sz[O_PROF], s));
+        prof.start(PK_INIT, s);
+    }
+    for (int i = 0; i < S; ++i) {
+        const SetSpec &x = *sets[i];
+        const int ws0 = i * Ws;
+        if (x.init_planes) {
+            const uint32_t *src = x.init_planes;
             if (host_out) {
-                uint32_t *stage = (uint32_t *)(ws + off[O_PLANES]);
-                FSGP_CUDA(cudaMemcpyAsync(stage, src, sz[O_PLANES], cudaMemcpyHostToDevice, s));
+                uint32_t *stage = (uint32_t *)(ws + off[O_PLANES]) + planes_off[i];
+                FSGP_CUDA(cudaMemcpyAsync(stage, src, sizeof(uint32_t) * (size_t)P * n * hp[i].W,
+                                          cudaMemcpyHostToDevice, s));
                 src = stage;
             }
             k_import<<<grid_cap((int64_t)P * n * Ws, 256, g->sm_count, 16), 256, 0, s>>>(
-                src, P, n, W, Ws, last_mask, buf0, buf1);
+                src, P, n, hp[i].W, Ws, Wn, ws0, hp[i].last_mask, buf0, buf1);
             ++launches;
-        } else {
-            const int64_t ns = seed_offsets[set + 1] - seed_offsets[set];
-            const int32_t *sd = seed_nodes + seed_offsets[set];
-            if (ns > 0) {
-                if (seed_flags == FSGP_PTR_HOST) {
-                    int32_t *stage = (int32_t *)(ws + off[O_SEEDS]) + seed_offsets[set];
-                    FSGP_CUDA(cudaMemcpyAsync(stage, sd, sizeof(int32_t) * (size_t)ns, cudaMemcpyHostToDevice, s));
-                    sd = stage;
-                }
-                k_seed<<<grid_cap(ns * Ws, 256, g->sm_count, 16), 256, 0, s>>>(
-                    buf0, buf1, A.plane_words, model != FSGP_SIR && model != FSGP_SIS, sd, ns, Ws, W, last_mask);
-                ++launches;
+        } else if (x.n_seeds > 0) {
+            const int32_t *sd = x.seeds;
+            if (x.seed_flags == FSGP_PTR_HOST) {
+                int32_t *stage = (int32_t *)(ws + off[O_SEEDS]) + seed_off[i];
+                FSGP_CUDA(cudaMemcpyAsync(stage, sd, sizeof(int32_t) * (size_t)x.n_seeds,
+                                          cudaMemcpyHostToDevice, s));
+                sd = stage;
             }
-        }
-        // step 0
-        A.cur = buf0;
-        A.nxt = buf1;
-        A.pc = pc;
-        A.k = 0;
-        A.t = (uint32_t)opt.t0;
-        A.list_in = list[1];
-        A.list_out = list[0];
-        k_init_scan<<<grid_scan, kBlock, smem_lanes, s>>>(A, model);
-        ++launches;
-        if (profiling) prof.stop(s);
-        FSGP_CUDA(cudaGetLastError());
-        for (int k = 1; k <= T; ++k) {
-            A.k = k;
-            A.t = (uint32_t)(opt.t0 + k);
-            A.cur = (k & 1) ? buf0 : buf1;
-            A.nxt = (k & 1) ? buf1 : buf0;
-            A.pc = pc + 2 * (size_t)k;
-            A.list_in = list[(k - 1) & 1];
-            A.list_out = list[k & 1];
-            const int force_dense = !allow_sparse || (k == 1 && use_init && model == FSGP_LT);
-            if (profiling) prof.start(PK_BEGIN, s);
-            k_begin<<<preal_d ? std::max(1, (R + 255) / 256) : 1, 256, 0, s>>>(
-                A, model, sparse_limit, force_dense, preal_d, R, (int)T1);
-            if (profiling) prof.stop(s);
-            if (allow_sparse) {
-                if (profiling) prof.start(PK_MARK, s);
-                k_mark<<<grid_mark, kBlock, 0, s>>>(A);
-                if (profiling) prof.stop(s);
-            }
-            rc = launch_rows_model(model, A, L, s);
-            if (rc) return rc;
-            launches += 1 + (allow_sparse ? 1 : 0) + (L.have_hub ? 2 : 0) + (L.have_mid ? 1 : 0) +
-                        (L.have_small ? 1 : 0);
-        }
-        FSGP_CUDA(cudaGetLastError());
-        if (profiling) prof.start(PK_RESULTS, s);
-        k_finalize<<<std::max(1, (int)((std::max<size_t>(T1, (size_t)R) + 255) / 256)), 256, 0, s>>>(
-            A, model, T, (unsigned long long)n * (unsigned long long)R, pc, counts_d, steps_d, preal_d, R);
-        if (freq_d)
-            k_freq<<<grid_cap(n, 256, g->sm_count, 16), 256, 0, s>>>(A, model, buf0, buf1, R, freq_d);
-        if (planes_d)
-            k_export<<<grid_cap((int64_t)P * n * W, 256, g->sm_count, 16), 256, 0, s>>>(A, P, buf0, buf1, planes_d);
-        if (profiling) prof.stop(s);
-        launches += 1 + (freq_d ? 1 : 0) + (planes_d ? 1 : 0);
-        FSGP_CUDA(cudaGetLastError());
-        if (profiling) {
-            unsigned long long hb[FSGP_PROF_KINDS];
-            Ctl hc;
-            FSGP_CUDA(cudaMemcpyAsync(hb, d_prof, sizeof hb, cudaMemcpyDeviceToHost, s));
-            FSGP_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof hc, cudaMemcpyDeviceToHost, s));
-            FSGP_CUDA(cudaStreamSynchronize(s));
-            fsgp_profile *pf = opt.profile;
-            for (size_t i = 0; i + 1 < prof.ev.size(); i += 2) {
-                float ms = 0.f;
-                FSGP_CUDA(cudaEventElapsedTime(&ms, prof.ev[i], prof.ev[i + 1]));
-                const int kd = prof.kind[i];
-                pf->ms[kd] += ms;
-                pf->launches[kd] += 1;
-            }
-            for (cudaEvent_t e : prof.ev) cudaEventDestroy(e);
-            prof.ev.clear();
-            prof.kind.clear();
-            for (int i = 0; i < FSGP_PROF_KINDS; ++i) pf->alg_bytes[i] += (double)hb[i];
-            pf->dense_steps += hc.dense_steps;
-            pf->sparse_steps += hc.sparse_steps;
-            pf->kernel_launches += launches;
-            launches = 0;
-        }
-        if (host_out) {
-            FSGP_CUDA(cudaMemcpyAsync(out->counts + (size_t)set * T1 * 3, counts_d, T1 * 3 * sizeof(uint64_t),
-                                      cudaMemcpyDeviceToHost, s));
-            if (freq_d)
-                FSGP_CUDA(cudaMemcpyAsync(out->freq + (size_t)set * 3 * n, freq_d, 3 * (size_t)n * sizeof(uint32_t),
-                                          cudaMemcpyDeviceToHost, s));
-            if (preal_d)
-                FSGP_CUDA(cudaMemcpyAsync(out->per_real + (size_t)set * R * T1 * 3, preal_d,
-                                          (size_t)R * T1 * 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-            if (planes_d)
-                FSGP_CUDA(cudaMemcpyAsync(out->final_planes + (size_t)set * P * n * W, planes_d,
-                                          (size_t)P * n * W * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-            if (out->steps_run) {
-                Ctl hc;
-                FSGP_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-                FSGP_CUDA(cudaStreamSynchronize(s));
-                out->steps_run[set] = hc.steps_done;
-            }
-            FSGP_CUDA(cudaStreamSynchronize(s));
+            k_seed<<<grid_cap(x.n_seeds * Ws, 256, g->sm_count, 16), 256, 0, s>>>(
+                buf0, buf1, A.plane_words, model != FSGP_SIR && model != FSGP_SIS, sd, x.n_seeds,
+                Wn, ws0, Ws, hp[i].W, hp[i].last_mask);
+            ++launches;
         }
     }
+    // step 0
+    A.cur = buf0;
+    A.nxt = buf1;
+    A.pc = pc;
+    A.k = 0;
+    A.t = (uint32_t)opt.t0;
+    A.list_in = list[1];
+    A.list_out = list[0];
+    k_init_scan<<<grid_scan, kBlock, smem_lanes, s>>>(A, model);
+    ++launches;
+    if (profiling) prof.stop(s);
     FSGP_CUDA(cudaGetLastError());
+    for (int k = 1; k <= T; ++k) {
+        A.k = k;
+        A.t = (uint32_t)(opt.t0 + k);
+        A.cur = (k & 1) ? buf0 : buf1;
+        A.nxt = (k & 1) ? buf1 : buf0;
+        A.pc = pc + (size_t)k * S * 2;
+        A.list_in = list[(k - 1) & 1];
+        A.list_out = list[k & 1];
+        const int force_dense = !allow_sparse || (k == 1 && any_init && model == FSGP_LT);
+        if (profiling) prof.start(PK_BEGIN, s);
+        k_begin<<<want_lanes ? std::max(1, (Wn * 32 + 255) / 256) : 1, 256, 0, s>>>(
+            A, model, sparse_limit, force_dense, d_out, (int)T1);
+        if (profiling) prof.stop(s);
+        if (allow_sparse) {
+            if (profiling) prof.start(PK_MARK, s);
+            k_mark<<<grid_mark, kBlock, 0, s>>>(A);
+            if (profiling) prof.stop(s);
+        }
+        rc = launch_rows_model(model, A, L, s);
+        if (rc) return rc;
+        launches += 1 + (allow_sparse ? 1 : 0) + (L.have_hub ? 2 : 0) + (L.have_mid ? 1 : 0) +
+                    (L.have_small ? 1 : 0);
+    }
+    FSGP_CUDA(cudaGetLastError());
+    if (profiling) prof.start(PK_RESULTS, s);
+    const int64_t fin_work = std::max<int64_t>((int64_t)T1 * S, (int64_t)Wn * 32);
+    k_finalize<<<(int)std::max<int64_t>(1, std::min<int64_t>(1024, (fin_work + 255) / 256)), 256, 0, s>>>(
+        A, model, T, pc, d_out);
+    ++launches;
+    if (want_freq) {
+        k_freq<<<grid_cap(n, 256, g->sm_count, 16), 256, 0, s>>>(A, model, buf0, buf1, d_out);
+        ++launches;
+    }
+    for (int i = 0; i < S; ++i) {
+        if (!ho[i].planes) continue;
+        k_export<<<grid_cap((int64_t)P * n * hp[i].W, 256, g->sm_count, 16), 256, 0, s>>>(
+            A, P, i * Ws, hp[i].W, buf0, buf1, ho[i].planes);
+        ++launches;
+    }
+    if (profiling) prof.stop(s);
+    FSGP_CUDA(cudaGetLastError());
+
+    // steps run: IC/LT report the first step whose frontier is empty in every... set of
+    // its own (read back from the per-set plane counts); SIR/SIS run all T steps
+    std::vector<unsigned long long> hpc;
+    if (want_steps && (model == FSGP_IC || model == FSGP_LT)) {
+        hpc.resize(T1 * S * 2);
+        FSGP_CUDA(cudaMemcpyAsync(hpc.data(), pc, sz[O_PC], cudaMemcpyDeviceToHost, s));
+    }
+    if (host_out) {
+        for (int i = 0; i < S; ++i) {
+            const SetSpec &x = *sets[i];
+            FSGP_CUDA(cudaMemcpyAsync(x.counts, ho[i].counts, T1 * 3 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+            if (x.freq)
+                FSGP_CUDA(cudaMemcpyAsync(x.freq, ho[i].freq, 3 * (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+            if (x.per_real)
+                FSGP_CUDA(cudaMemcpyAsync(x.per_real, ho[i].per_real, (size_t)x.R * T1 * 3 * sizeof(uint32_t),
+                                          cudaMemcpyDeviceToHost, s));
+            if (x.final_planes)
+                FSGP_CUDA(cudaMemcpyAsync(x.final_planes, ho[i].planes, (size_t)P * n * hp[i].W * sizeof(uint32_t),
+                                          cudaMemcpyDeviceToHost, s));
+        }
+    }
+    if (want_steps || host_out || profiling) FSGP_CUDA(cudaStreamSynchronize(s));
+    if (want_steps) {
+        std::vector<int32_t> st((size_t)S, T);
+        for (int i = 0; i < S; ++i) {
+            if (model == FSGP_IC || model == FSGP_LT)
+                for (int k = 0; k <= T; ++k)
+                    if (hpc[((size_t)k * S + i) * 2 + 1] == 0ull) {
+                        st[i] = k;
+                        break;
+                    }
+            if (!sets[i]->steps_run) continue;
+            if (host_out) *sets[i]->steps_run = st[i];
+            else FSGP_CUDA(cudaMemcpyAsync(sets[i]->steps_run, &st[i], sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        }
+        if (!host_out) FSGP_CUDA(cudaStreamSynchronize(s));
+    }
+    if (profiling) {
+        unsigned long long hb[FSGP_PROF_KINDS];
+        Ctl hc;
+        FSGP_CUDA(cudaMemcpyAsync(hb, d_prof, sizeof hb, cudaMemcpyDeviceToHost, s));
+        FSGP_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof hc, cudaMemcpyDeviceToHost, s));
+        FSGP_CUDA(cudaStreamSynchronize(s));
+        fsgp_profile *pf = opt.profile;
+        for (size_t i = 0; i + 1 < prof.ev.size(); i += 2) {
+            float ms = 0.f;
+            FSGP_CUDA(cudaEventElapsedTime(&ms, prof.ev[i], prof.ev[i + 1]));
+            const int kd = prof.kind[i];
+            pf->ms[kd] += ms;
+            pf->launches[kd] += 1;
+        }
+        for (cudaEvent_t e : prof.ev) cudaEventDestroy(e);
+        for (int i = 0; i < FSGP_PROF_KINDS; ++i) pf->alg_bytes[i] += (double)hb[i];
+        pf->dense_steps += hc.dense_steps;
+        pf->sparse_steps += hc.sparse_steps;
+        pf->kernel_launches += launches;
+    }
     return FSGP_OK;
+}
+
+int run_sets(fsgp_graph *g, int model, int ic_mode, const SetSpec *sets, int n_sets, int T,
+             const fsgp_options &opt, cudaStream_t s) {
+    if (n_sets < 1) return FSGP_OK;
+    const uint32_t of = sets[0].out_flags;
+    for (int i = 0; i < n_sets; ++i) {
+        const SetSpec &x = sets[i];
+        if (x.R < 1 || x.R > kMaxR) return fail(FSGP_EINVAL, "R must be in [1, 4096]");
+        if (!x.counts) return fail(FSGP_EINVAL, "result counts buffer is NULL");
+        if (x.out_flags != of) return fail(FSGP_EINVAL, "all result buffers of one call must be host or all device");
+        auto bad_p = [](double p) { return !(p >= 0.0 && p <= 1.0); };
+        if (bad_p(x.beta) || bad_p(x.gamma) || bad_p(x.ic_p))
+            return fail(FSGP_EINVAL, "probabilities must lie in [0, 1]");
+        if (!x.init_planes && x.n_seeds > 0) {
+            if (!x.seeds) return fail(FSGP_EINVAL, "seed_nodes is NULL");
+            std::vector<int32_t> host_copy;
+            const int32_t *hs = x.seeds;
+            if (x.seed_flags == FSGP_PTR_DEVICE) {
+                host_copy.resize((size_t)x.n_seeds);
+                FSGP_CUDA(cudaMemcpy(host_copy.data(), x.seeds, sizeof(int32_t) * (size_t)x.n_seeds,
+                                     cudaMemcpyDeviceToHost));
+                hs = host_copy.data();
+            }
+            for (int64_t j = 0; j < x.n_seeds; ++j)
+                if (hs[j] < 0 || hs[j] >= g->n) return fail(FSGP_EINVAL, "seed node out of range");
+        }
+    }
+    // group by words per set, then waves of at most kMaxSets sets that fit the state
+    // budget and, when per-realization counts are wanted, the shared-memory lane counters
+    std::vector<int> order((size_t)n_sets);
+    for (int i = 0; i < n_sets; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return words_per_set(sets[a].R) < words_per_set(sets[b].R);
+    });
+    const int P = fsgp_model_planes(model);
+    const size_t budget = (size_t)48 << 30;   // bytes of double-buffered state per wave
+    size_t i = 0;
+    while (i < order.size()) {
+        const int Ws = words_per_set(sets[order[i]].R);
+        const size_t per_set_state = 2ull * P * (size_t)g->n * Ws * sizeof(uint32_t);
+        const int smax = (int)std::max<size_t>(
+            1, std::min<size_t>(kMaxSets, budget / std::max<size_t>(per_set_state, 1)));
+        std::vector<const SetSpec *> wave;
+        bool lanes = false;
+        while (i < order.size() && words_per_set(sets[order[i]].R) == Ws && (int)wave.size() < smax) {
+            const SetSpec *x = &sets[order[i]];
+            const bool l2 = lanes || x->per_real;
+            if (l2 && !wave.empty() && (int)(wave.size() + 1) * Ws > 128) break;   // 32 KB of lane counters
+            lanes = l2;
+            wave.push_back(x);
+            ++i;
+        }
+        const int rc = run_wave(g, model, ic_mode, wave.data(), (int)wave.size(), Ws, T, opt, s);
+        if (rc) return rc;
+    }
+    return FSGP_OK;
+}
+
+}  // namespace fsgp
+
+using namespace fsgp;
+
+extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_params *params,
+                             const int32_t *seed_nodes, const int64_t *seed_offsets,
+                             int32_t n_sets, uint32_t seed_flags, int32_t R, int32_t T,
+                             uint64_t rng_seed, const fsgp_options *opt_in, fsgp_result *out,
+                             void *stream) {
+    set_error("");
+    fsgp_graph *g = const_cast<fsgp_graph *>(gc);
+    if (!g) return fail(FSGP_EINVAL, "graph is NULL");
+    if (model < FSGP_SIR || model > FSGP_LT) return fail(FSGP_EINVAL, "unknown model");
+    if (!params) return fail(FSGP_EINVAL, "params is NULL");
+    if (!out || !out->counts) return fail(FSGP_EINVAL, "result counts buffer is NULL");
+    if (out->flags != FSGP_PTR_HOST && out->flags != FSGP_PTR_DEVICE)
+        return fail(FSGP_EINVAL, "bad result flags");
+    if (R < 1 || R > kMaxR) return fail(FSGP_EINVAL, "R must be in [1, 4096]");
+    if (T < 0) return fail(FSGP_EINVAL, "T must be >= 0");
+    if (n_sets < 1) return fail(FSGP_EINVAL, "n_sets must be >= 1");
+    if (params->ic_mode != FSGP_IC_WEIGHTED_CASCADE && params->ic_mode != FSGP_IC_CONSTANT)
+        return fail(FSGP_EINVAL, "bad ic_mode");
+    fsgp_options opt{};
+    if (opt_in) opt = *opt_in;
+    if (opt.r_offset < 0 || (opt.r_offset & 31)) return fail(FSGP_EINVAL, "r_offset must be a non-negative multiple of 32");
+    if (opt.t0 < 0) return fail(FSGP_EINVAL, "t0 must be >= 0");
+    if ((int64_t)opt.t0 + T > (int64_t)UINT32_MAX) return fail(FSGP_EINVAL, "t0 + T too large");
+    const bool use_init = opt.init_planes != nullptr;
+    if (!use_init) {
+        if (!seed_offsets) return fail(FSGP_EINVAL, "seed_offsets is NULL");
+        if (seed_flags != FSGP_PTR_HOST && seed_flags != FSGP_PTR_DEVICE) return fail(FSGP_EINVAL, "bad seed flags");
+        if (seed_offsets[0] != 0) return fail(FSGP_EINVAL, "seed_offsets[0] must be 0");
+        for (int s = 0; s < n_sets; ++s)
+            if (seed_offsets[s + 1] < seed_offsets[s]) return fail(FSGP_EINVAL, "seed_offsets must be non-decreasing");
+        if (seed_offsets[n_sets] > 0 && !seed_nodes) return fail(FSGP_EINVAL, "seed_nodes is NULL");
+    }
+    int dev = 0;
+    FSGP_CUDA(cudaGetDevice(&dev));
+    if (dev != g->device) return fail(FSGP_EINVAL, "current device differs from the graph's device");
+    const int P = fsgp_model_planes(model);
+    const int W = (R + 31) / 32;
+    const size_t T1 = (size_t)T + 1;
+    std::vector<SetSpec> sets((size_t)n_sets);
+    for (int i = 0; i < n_sets; ++i) {
+        SetSpec &x = sets[i];
+        x = SetSpec{};
+        x.beta = params->beta;
+        x.gamma = params->gamma;
+        x.ic_p = params->ic_p;
+        x.rng_seed = rng_seed;
+        x.R = R;
+        if (use_init) {
+            x.init_planes = opt.init_planes + (size_t)i * P * g->n * W;
+        } else {
+            x.seeds = seed_nodes ? seed_nodes + seed_offsets[i] : nullptr;
+            x.n_seeds = seed_offsets[i + 1] - seed_offsets[i];
+            x.seed_flags = seed_flags;
+        }
+        x.counts = out->counts + (size_t)i * T1 * 3;
+        x.freq = out->freq ? out->freq + (size_t)i * 3 * g->n : nullptr;
+        x.per_real = out->per_real ? out->per_real + (size_t)i * R * T1 * 3 : nullptr;
+        x.final_planes = out->final_planes ? out->final_planes + (size_t)i * P * g->n * W : nullptr;
+        x.steps_run = out->steps_run ? out->steps_run + i : nullptr;
+        x.out_flags = out->flags;
+    }
+    return run_sets(g, model, params->ic_mode, sets.data(), n_sets, T, opt, (cudaStream_t)stream);
 }

@@ -7,8 +7,12 @@
 // realizations per 32-bit word, one bit per lane, one plane per indicator vector.
 //
 // Work decomposition (GB300-specific, not from the paper):
-//   * a "team" of TEAM threads covers all Ws words of one node, V words per thread
-//     (128-bit loads when V = 4);
+//   * several seed sets (or batched requests) can run side by side: set s owns words
+//     [s*Ws, (s+1)*Ws) of every node, with its own randomness key, thresholds and
+//     valid-lane mask, so each set's result equals a run of that set alone;
+//   * a "team" of TEAM threads covers a slice of TEAM*V words of one node, V words per
+//     thread (64-bit loads when V = 2, 128-bit when V = 4); a node of Wn = S*Ws words
+//     has Wn / (TEAM*V) slices, each an independent work item;
 //   * small rows: one team per row (a warp holds 32/TEAM rows of similar degree, the
 //     rows come bucketed by degree);
 //   * mid rows: one warp per row, arcs interleaved over the warp's teams, counters
@@ -40,6 +44,18 @@ struct Ctl {
     int32_t list_valid[2]; // the list of that parity was built
 };
 
+// Per-set parameters (device array, one entry per set of the launch).
+struct SetParams {
+    uint32_t key0, key1;            // rng seed
+    const uint64_t *surv;           // survival table (SIR/SIS)
+    int32_t ksat;                   // first k with surv[k] = 0, or INT32_MAX
+    int32_t W;                      // words holding valid lanes, ceil(R/32)
+    uint32_t last_mask;             // valid lanes of word W-1
+    int32_t R;
+    uint64_t g_rec;                 // recovery threshold
+    uint64_t p_const;               // IC constant threshold
+};
+
 struct StepArgs {
     // graph
     const int32_t *__restrict__ row_ptr;
@@ -47,30 +63,27 @@ struct StepArgs {
     const int32_t *__restrict__ out_ptr;
     const int32_t *__restrict__ out_dst;
     int32_t n;
-    int32_t Ws;            // words per node in the state arrays (power of two)
-    int32_t W;             // words holding valid lanes, ceil(R/32)
-    uint32_t last_mask;    // valid lanes of word W-1
-    uint32_t gbase;        // global word index of word 0 (realization offset / 32)
+    int32_t Ws;            // words per set (power of two)
+    int32_t ws_shift;      // log2(Ws)
+    int32_t S;             // sets in this launch
+    int32_t Wn;            // words per node = S * Ws
+    int32_t nslices;       // work items per row = Wn / (TEAM * V)
+    uint32_t gbase;        // global word index of word 0 of a set (realization offset / 32)
     int32_t small_max_deg; // 2^k - 1
     int32_t hub_min_deg;   // power of two
-    // state: [planes][n][Ws] per buffer
+    // state: [planes][n][Wn] per buffer
     const uint32_t *__restrict__ cur;
     uint32_t *__restrict__ nxt;
-    size_t plane_words;    // n * Ws
+    size_t plane_words;    // n * Wn
     // model parameters
-    const uint64_t *__restrict__ surv;  // survival table surv[0..surv_last]
-    int32_t surv_last;
-    int32_t ksat;          // first k with surv[k] = 0, or INT32_MAX
-    uint64_t g_rec;        // recovery threshold
-    uint64_t p_const;      // IC constant threshold
+    const SetParams *__restrict__ sp;   // [S]
     int32_t ic_mode;
-    uint32_t key0, key1;
     uint32_t t;            // absolute step index of the step being computed
     int32_t k;             // relative step index (1..T)
     // control and accumulators
     Ctl *ctl;
-    unsigned long long *pc;        // [2] plane popcounts of this step (running totals)
-    int32_t *lane_cnt;             // [2][Wpad*32] running per-lane plane counts, or null
+    unsigned long long *pc;        // [S][2] plane popcounts of this step (running totals)
+    int32_t *lane_cnt;             // [2][Wn*32] running per-lane plane counts, or null
     // row lists
     const int32_t *__restrict__ rows_small;
     const int32_t *__restrict__ rows_mid;
@@ -86,7 +99,7 @@ struct StepArgs {
     int32_t n_hubs;
     int64_t n_hub_chunks;
     int32_t hub_chunk;
-    uint32_t *hub_scratch;          // [n_hubs][Ws*32] per-lane counts (IC: [n_hubs][Ws] masks)
+    uint32_t *hub_scratch;          // [n_hubs][Wn*32] per-lane counts (IC: [n_hubs][Wn] masks)
     unsigned long long *prof_bytes; // [8] algorithmic bytes per kernel kind, or null
 };
 
@@ -94,17 +107,33 @@ struct StepArgs {
 enum { PK_INIT = 0, PK_BEGIN = 1, PK_MARK = 2, PK_HUB = 3, PK_HUBFIN = 4, PK_MID = 5,
        PK_SMALL = 6, PK_RESULTS = 7 };
 
-// Algorithmic bytes of one row: row pointers, own state read + written, and per
-// gathered in-arc the column index plus the source's state words (at least a sector).
-__device__ __forceinline__ unsigned long long row_bytes(const StepArgs &A, int planes,
-                                                        bool gathered, int64_t deg) {
-    const unsigned long long own = 2ull * planes * 4ull * (unsigned long long)A.Ws;
-    const unsigned long long src = A.Ws * 4 > 32 ? (unsigned long long)A.Ws * 4ull : 32ull;
+// Algorithmic bytes of one work item (a slice of `words` words of one row): row pointers,
+// own state read + written, and per gathered in-arc the column index plus the source's
+// words of the slice (at least one 32-byte sector).
+__device__ __forceinline__ unsigned long long row_bytes(int words, int planes, bool gathered,
+                                                        int64_t deg) {
+    const unsigned long long own = 2ull * planes * 4ull * (unsigned long long)words;
+    const unsigned long long src = words * 4 > 32 ? (unsigned long long)words * 4ull : 32ull;
     return 8ull + own + (gathered ? (unsigned long long)deg * (4ull + src) : 0ull);
 }
 
-__device__ __forceinline__ uint32_t word_valid_mask(const StepArgs &A, int w) {
-    return w < A.W - 1 ? 0xffffffffu : (w == A.W - 1 ? A.last_mask : 0u);
+// Everything one state word needs: its set, Philox word index, valid lanes, key.
+struct WordCtx {
+    int s;
+    uint32_t g, vm, k0, k1;
+};
+
+__device__ __forceinline__ WordCtx word_ctx(const StepArgs &A, int w) {
+    WordCtx c;
+    c.s = w >> A.ws_shift;
+    const int wl = w & (A.Ws - 1);
+    const SetParams &p = A.sp[c.s];
+    const int W = __ldg(&p.W);
+    c.vm = wl < W - 1 ? 0xffffffffu : (wl == W - 1 ? __ldg(&p.last_mask) : 0u);
+    c.g = A.gbase + (uint32_t)wl;
+    c.k0 = __ldg(&p.key0);
+    c.k1 = __ldg(&p.key1);
+    return c;
 }
 
 // ------------------------------------------------------------ bit-sliced counters
@@ -320,26 +349,27 @@ struct WordOut {
 
 // SIR / SIS word update from counts of infected in-arcs (Appendix A.1 rules).
 template <int MODEL, int B>
-__device__ __forceinline__ WordOut update_sir_word(const StepArgs &A, uint32_t v, uint32_t g,
-                                                   uint32_t vm, uint32_t s0, uint32_t s1,
-                                                   const uint32_t (&c)[B]) {
-    const uint32_t S = vm & ~s0 & ~s1;
+__device__ __forceinline__ WordOut update_sir_word(const StepArgs &A, uint32_t v, const WordCtx &x,
+                                                   uint32_t s0, uint32_t s1, const uint32_t (&c)[B]) {
+    const SetParams &p = A.sp[x.s];
+    const uint32_t S = x.vm & ~s0 & ~s1;
     const uint32_t cand = S & any_count<B>(c);
     uint32_t infect = 0u;
     if (cand) {
+        const int32_t ksat = __ldg(&p.ksat);
         uint32_t sat = 0u;
-        if ((uint64_t)A.ksat < (1ull << B)) sat = ge_const<B>(c, (uint32_t)A.ksat) & cand;
+        if ((uint64_t)ksat < (1ull << B)) sat = ge_const<B>(c, (uint32_t)ksat) & cand;
         const uint32_t rem = cand & ~sat;
         uint32_t below = 0u;
         if (rem) {
-            const uint64_t *surv = A.surv;
+            const uint64_t *surv = p.surv;
             below = grouped_u_less<B>(c, rem, [surv](uint32_t k) { return __ldg(surv + k); }, v,
-                                      A.t, g, TAG_INFECT, A.key0, A.key1);
+                                      A.t, x.g, TAG_INFECT, x.k0, x.k1);
         }
         infect = sat | (rem & ~below);   // infected iff u >= surv[k]
     }
-    const uint32_t I = s0 & vm;
-    const uint32_t rec = lanes_u_less(I, A.g_rec, v, A.t, g, TAG_RECOVER, A.key0, A.key1);
+    const uint32_t I = s0 & x.vm;
+    const uint32_t rec = lanes_u_less(I, __ldg(&p.g_rec), v, A.t, x.g, TAG_RECOVER, x.k0, x.k1);
     WordOut o;
     o.n0 = (s0 & ~rec) | infect;
     o.n1 = MODEL == FSGP_SIR ? (s1 | rec) : 0u;
@@ -348,10 +378,9 @@ __device__ __forceinline__ WordOut update_sir_word(const StepArgs &A, uint32_t v
 
 // LT word update from counts of active in-arcs: activate iff k*2^32 >= theta*d.
 template <int B>
-__device__ __forceinline__ WordOut update_lt_word(const StepArgs &A, uint32_t v, uint32_t g,
-                                                  uint32_t vm, uint32_t s0, int32_t d,
-                                                  const uint32_t (&c)[B]) {
-    const uint32_t cand = vm & ~s0 & any_count<B>(c);
+__device__ __forceinline__ WordOut update_lt_word(const StepArgs &A, uint32_t v, const WordCtx &x,
+                                                  uint32_t s0, int32_t d, const uint32_t (&c)[B]) {
+    const uint32_t cand = x.vm & ~s0 & any_count<B>(c);
     uint32_t act = 0u;
     if (cand) {
         uint32_t sat = 0u;
@@ -361,7 +390,7 @@ __device__ __forceinline__ WordOut update_lt_word(const StepArgs &A, uint32_t v,
             const uint64_t dd = (uint64_t)d;
             act = grouped_u_less<B>(c, rem,
                                     [dd](uint32_t k) { return ((uint64_t)k << 32) / dd + 1ull; },
-                                    v, 0u, g, TAG_LT_THRESH, A.key0, A.key1);
+                                    v, 0u, x.g, TAG_LT_THRESH, x.k0, x.k1);
         }
         act |= sat;
     }
@@ -375,10 +404,28 @@ __device__ __forceinline__ WordOut update_lt_word(const StepArgs &A, uint32_t v,
 
 // Per-thread running sums, flushed once per CTA.
 struct Accum {
-    long long d0 = 0, d1 = 0;
     unsigned long long push_deg = 0;
     unsigned long long bytes = 0;
 };
+
+// Per-set plane-popcount changes of one CTA live in shared memory (kMaxSets x 2).
+constexpr int kMaxSets = 128;
+
+__device__ __forceinline__ void set_acc_zero(unsigned long long *s_pc, int S) {
+    for (int i = threadIdx.x; i < 2 * S; i += blockDim.x) s_pc[i] = 0ull;
+    __syncthreads();
+}
+
+__device__ __forceinline__ void set_acc_add(unsigned long long *s_pc, int s, long long d0, long long d1) {
+    if (d0) atomicAdd(&s_pc[2 * s], (unsigned long long)d0);
+    if (d1) atomicAdd(&s_pc[2 * s + 1], (unsigned long long)d1);
+}
+
+// after a __syncthreads of the caller
+__device__ __forceinline__ void set_acc_flush(const StepArgs &A, const unsigned long long *s_pc) {
+    for (int i = threadIdx.x; i < 2 * A.S; i += blockDim.x)
+        if (s_pc[i]) atomicAdd(&A.pc[i], s_pc[i]);
+}
 
 // per-lane count changes of one word of one plane (s_plane: that plane's counters)
 __device__ __forceinline__ void lane_deltas(int32_t *s_plane, int w, uint32_t olds, uint32_t news) {
@@ -395,14 +442,12 @@ __device__ __forceinline__ void flush_accum(const StepArgs &A, Accum acc, int li
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        acc.d0 += __shfl_xor_sync(0xffffffffu, acc.d0, o);
-        acc.d1 += __shfl_xor_sync(0xffffffffu, acc.d1, o);
         acc.push_deg += __shfl_xor_sync(0xffffffffu, acc.push_deg, o);
         acc.bytes += __shfl_xor_sync(0xffffffffu, acc.bytes, o);
     }
     if (lane == 0) {
-        s_red[0][wid] = acc.d0;
-        s_red[1][wid] = acc.d1;
+        s_red[0][wid] = 0;
+        s_red[1][wid] = 0;
         s_red[2][wid] = (long long)acc.push_deg;
         s_red[3][wid] = (long long)acc.bytes;
     }
@@ -415,9 +460,9 @@ __device__ __forceinline__ void flush_accum(const StepArgs &A, Accum acc, int li
             c += s_red[2][i];
             d += s_red[3][i];
         }
+        (void)a;
+        (void)b;
         if (A.prof_bytes && d) atomicAdd(&A.prof_bytes[kind], (unsigned long long)d);
-        if (a) atomicAdd(&A.pc[0], (unsigned long long)a);
-        if (b) atomicAdd(&A.pc[1], (unsigned long long)b);
         if (c) atomicAdd((unsigned long long *)&A.ctl->push_outdeg[list_slot], (unsigned long long)c);
     }
 }
@@ -447,7 +492,7 @@ __device__ __forceinline__ void list_append(const StepArgs &A, bool want, int32_
 
 // Launch shape of the row kernels of one step (host side).
 struct StepLaunch {
-    int V, TEAM;
+    int V, TEAM;           // words per thread, threads per slice team
     int grid_small, grid_mid, grid_hub, grid_fin;
     size_t smem_lanes;     // dynamic shared memory for per-lane counters (0 = off)
     bool have_small, have_mid, have_hub;
@@ -467,6 +512,29 @@ struct Prof {
     }
     void stop(cudaStream_t s) { start(-1, s); }
 };
+
+// One seed set (or one batched request) of a run: parameters, inputs and caller-owned
+// outputs (memory kind out_flags; NULL = not wanted, except counts).
+struct SetSpec {
+    double beta, gamma, ic_p;
+    uint64_t rng_seed;
+    int32_t R;
+    const int32_t *seeds;          // seed nodes (memory kind seed_flags)
+    int64_t n_seeds;
+    uint32_t seed_flags;
+    const uint32_t *init_planes;   // optional start planes [P][n][ceil(R/32)]
+    uint64_t *counts;              // [T+1][3]
+    uint32_t *freq;                // [3][n]
+    uint32_t *per_real;            // [R][T+1][3]
+    uint32_t *final_planes;        // [P][n][ceil(R/32)]
+    int32_t *steps_run;            // [1]
+    uint32_t out_flags;
+};
+
+// Runs every set for T steps on graph g (simulate.cu).  Sets with the same words per
+// set run side by side in one launch sequence (up to kMaxSets at a time).
+int run_sets(fsgp_graph *g, int model, int ic_mode, const SetSpec *sets, int n_sets, int T,
+             const fsgp_options &opt, cudaStream_t s);
 
 // Defined in rows.cuh, instantiated once per model (model_*.cu).
 template <int MODEL>

@@ -265,3 +265,22 @@ def test_rmat20_sir_sis_lane_subset(cuda_lib):
             orc = O.simulate(model, g.row_ptr, g.col_idx, seeds, R=256, T=100, rng_seed=3,
                              beta=0.01, gamma=0.05, r_lo=lo, n_real=cnt)
             assert np.array_equal(gr["per_real"][0][lo:lo + cnt], orc.per_real), (model, lo)
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("R,n_sets", [(32, 5), (64, 130), (100, 3)])
+def test_stacked_seed_sets(cuda_lib, model, R, n_sets):
+    """Many seed sets run side by side in one launch sequence (waves of up to 128 sets,
+    odd set counts, 1-word sets): every set equals the oracle run of that set alone."""
+    g = W.ba(2500, 3, seed=121)
+    sets = [W.seed_set(g.n, 1 + (i % 7), seed=1000 + i) for i in range(n_sets)]
+    gr = gpu_run(cuda_lib, g, model, sets, R, 9, 51, **_prm(model))
+    check = sorted({0, 1, n_sets // 2, n_sets - 1})
+    for i in check:
+        orc = O.simulate(model, g.row_ptr, g.col_idx, sets[i], R=R, T=9, rng_seed=51, **_prm(model))
+        assert np.array_equal(gr["per_real"][i], orc.per_real), (model, i)
+        assert np.array_equal(gr["freq"][i], orc.freq), (model, i)
+        st = states_from_planes(model, gr["final_planes"][i], range(R))
+        assert np.array_equal(st, orc.final_state), (model, i)
+        if model in (O.IC, O.LT):
+            assert gr["steps_run"][i] == orc.quiet_step.max(), (model, i)
