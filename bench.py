@@ -220,6 +220,60 @@ def cpu_baseline(g, seeds):
                       f"{sec:.1f} s of CPU work"}
 
 
+# ---------------------------------------------------------------- batched requests
+
+def run_batch_bench(args):
+    """Batched requests: 64 BA/ER graphs with n log-uniform in 1k..2M, 4,096 requests
+    (model uniform over SIR/SIS/IC/LT, R in 32..1024, seed sets of 1..500 nodes, beta in
+    [0.005, 0.2], gamma 0.1, T = 100, IC/LT to quiescence), per-graph autotuning and
+    CUDA-graph capture.  One bench step = the whole batch.  Units are the
+    edge-realization-steps actually computed (IC/LT stop early)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2603_14895_gb300 import fsgp
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    graphs, reqs = W.batch_pool(n_graphs=args.batch_graphs, n_requests=args.batch_requests)
+    log(f"[bench] batch pool: {len(graphs)} graphs, {sum(g.nnz for g in graphs)} arcs, "
+        f"{len(reqs)} requests in {time.time() - t0:.1f}s")
+    gobjs = [fsgp.Graph(g.row_ptr, g.col_idx) for g in graphs]
+    spec = [dict(graph=gobjs[q.graph_index], model=q.model, seeds=q.seeds, R=q.R, T=q.T,
+                 rng_seed=q.rng_seed, beta=q.beta, gamma=q.gamma, freq=True) for q in reqs]
+    outs = None
+    t0 = time.time()
+    outs = fsgp.batch_run(spec, autotune=1)          # first run: tuning + allocation
+    torch.cuda.synchronize()
+    log(f"[bench] first batch (autotune) {time.time() - t0:.1f}s")
+    for _ in range(max(0, args.warmup - 1)):
+        fsgp.batch_run(spec)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(gpu_selector(torch))
+    sampler.start()
+    ev0.record()
+    for _ in range(args.steps):
+        outs = fsgp.batch_run(spec)
+    ev1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    steps = [int(o["steps_run"][0].item()) for o in outs]
+    units = sum(float(graphs[q.graph_index].nnz) * q.R * st for q, st in zip(reqs, steps))
+    nominal = sum(float(graphs[q.graph_index].nnz) * q.R * q.T for q in reqs)
+    return {"metric": "edge-realization-steps/sec", "value": units / (ms / 1e3),
+            "unit": "edge-realization-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"batch_{len(reqs)}req_{len(graphs)}graphs",
+                       "graphs": "BA m=2..8 and ER, n log-uniform 1k..2M",
+                       "requests": len(reqs), "models": "SIR/SIS/IC/LT", "R": "32..1024",
+                       "T": 100, "l2": "working set above L2 for the large graphs; no flush"},
+            "requests_per_s": len(reqs) / (ms / 1e3),
+            "nominal_units_per_s": nominal / (ms / 1e3),
+            "clocks": clocks}
+
+
 # ------------------------------------------------------------------------- main
 
 def main():
@@ -232,12 +286,19 @@ def main():
     ap.add_argument("--scale", type=int, default=SCALE)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="rmat26", choices=["rmat26", "batch"])
+    ap.add_argument("--batch-graphs", type=int, default=64)
+    ap.add_argument("--batch-requests", type=int, default=4096)
     args = ap.parse_args()
     SCALE = args.scale
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.workload == "batch" and args.impl == "fsgp":
+        print(json.dumps(run_batch_bench(args)), flush=True)
+        return
 
     if args.impl == "reference":
         if rank != 0:

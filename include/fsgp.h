@@ -124,7 +124,9 @@ typedef struct {
                                [n_sets][planes][n][ceil(R/32)] u32, same memory kind
                                as the result buffers (fsgp_result.flags) */
     fsgp_profile *profile;  /* optional host struct, accumulated (not cleared) */
-    int32_t reserved[8];
+    int32_t capture_graph;  /* 1: capture the step loop of each launch wave into a CUDA
+                               graph and launch it at once (ignored when profiling) */
+    int32_t reserved[7];
 } fsgp_options;
 
 /* Caller-owned result buffers, all host or all device (flags).  NULL = not wanted,
@@ -176,6 +178,49 @@ int fsgp_simulate(const fsgp_graph *g, int32_t model, const fsgp_params *params,
                   const int32_t *seed_nodes, const int64_t *seed_offsets, int32_t n_sets,
                   uint32_t seed_flags, int32_t R, int32_t T, uint64_t rng_seed,
                   const fsgp_options *opt, fsgp_result *out, void *stream);
+
+/* One request of a batch (fsgp_batch_run). */
+typedef struct {
+    const fsgp_graph *graph;
+    int32_t model;
+    fsgp_params params;
+    const int32_t *seed_nodes;   /* host array of n_seeds nodes (all R lanes start there) */
+    int64_t n_seeds;
+    int32_t R;                   /* 1..4096 realizations (lanes 0..R-1) */
+    int32_t T;
+    uint64_t rng_seed;
+    fsgp_result result;          /* device buffers only: result.flags = FSGP_PTR_DEVICE;
+                                    one set, layouts as in fsgp_result */
+} fsgp_request;
+
+typedef struct {
+    int32_t n_streams;      /* concurrent CUDA streams, one host thread each (0 = 4) */
+    int32_t capture_graph;  /* 0 (default) or 1: capture each launch wave's step loop into
+                               a CUDA graph; -1: launch kernels one by one */
+    int32_t autotune;       /* 1: run fsgp_autotune once per graph before its requests */
+    int32_t reserved[8];
+} fsgp_batch_options;
+
+/* Run many requests over a pool of graphs (batched Monte Carlo, Sec. 3.1, Eq. batch,
+ * across requests).  Requests on the same graph with the same model, IC mode and T run
+ * side by side in one launch sequence; each request keeps its own key, thresholds and
+ * lanes, so its results equal those of an fsgp_simulate call for it alone.  Graphs are
+ * spread over n_streams streams (longest first onto the least loaded), each issued by
+ * its own host thread.  Work is ordered after prior work on `stream`, and `stream`
+ * waits for all of it; the call returns once everything is enqueued.  A graph may
+ * appear in several requests but must not be used by other calls meanwhile.
+ * Errors: EINVAL (any bad request: nothing is run), ENOMEM, ECUDA. */
+int fsgp_batch_run(const fsgp_request *reqs, int32_t n, const fsgp_batch_options *opt,
+                   void *stream);
+
+/* Pick the tuning fields of *inout (vector_words, small_max_deg, hub_min_deg,
+ * hub_chunk) for graph g by timing short probe runs (T_probe steps from the given host
+ * seed set) of every candidate: words per thread {1, 2, 4}, team-row bound {63, 255},
+ * split-row bound {4096, 8192, 16384}.  Every candidate gives identical results; only
+ * speed differs.  Synchronises `stream`.  Errors: EINVAL, ENOMEM, ECUDA. */
+int fsgp_autotune(const fsgp_graph *g, int32_t model, const fsgp_params *params,
+                  const int32_t *seed_nodes, int64_t n_seeds, int32_t R, int32_t T_probe,
+                  uint64_t rng_seed, fsgp_options *inout, void *stream);
 
 /* One synchronous step (Eq. nodestate) of `model` that allocates no device memory.
  * The paper has no counterpart: this entry point exists for callers that cannot call

@@ -27,6 +27,7 @@ struct SetOut {
     uint32_t *freq;               // [3][n]
     uint32_t *per_real;           // [R][T+1][3]
     uint32_t *planes;             // [P][n][W]
+    int32_t *steps;               // [1] transitions computed (staging in the workspace)
 };
 
 // ------------------------------------------------------------------------ kernels
@@ -236,6 +237,17 @@ __global__ void k_finalize(StepArgs A, int model, int T, const unsigned long lon
         c[2] = (unsigned long long)o[2];
     }
     if (A.lane_cnt) snapshot_lanes(A, model, outs, T + 1, T);
+    // IC/LT: the first step whose frontier is empty (later rows repeat); SIR/SIS: T
+    for (int s = threadIdx.x + blockIdx.x * blockDim.x; s < S; s += blockDim.x * gridDim.x) {
+        int st = T;
+        if (model == FSGP_IC || model == FSGP_LT)
+            for (int k = 0; k <= T; ++k)
+                if (pc_all[((size_t)k * S + s) * 2 + 1] == 0ull) {
+                    st = k;
+                    break;
+                }
+        outs[s].steps[0] = st;
+    }
 }
 
 // Per-node final compartment frequencies of every set that asked for them.
@@ -476,7 +488,8 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     const size_t T1 = (size_t)T + 1;
     const size_t state_words = (size_t)P * n * Wn;
     enum { O_STATE, O_PC, O_CTL, O_LIST0, O_LIST1, O_CSMALL, O_CMID, O_BITMAP, O_LANES,
-           O_HUB, O_SURV, O_SEEDS, O_COUNTS, O_FREQ, O_PREAL, O_PLANES, O_PROF, O_SP, O_OUT, O_END };
+           O_HUB, O_SURV, O_SEEDS, O_COUNTS, O_FREQ, O_PREAL, O_PLANES, O_PROF, O_SP, O_OUT,
+           O_STEPS, O_END };
     size_t sz[O_END] = {0};
     sz[O_STATE] = 2 * state_words * sizeof(uint32_t);
     sz[O_PC] = T1 * S * 2 * sizeof(unsigned long long);
@@ -495,6 +508,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     sz[O_PROF] = FSGP_PROF_KINDS * sizeof(unsigned long long);
     sz[O_SP] = (size_t)S * sizeof(SetParams);
     sz[O_OUT] = (size_t)S * sizeof(SetOut);
+    sz[O_STEPS] = (size_t)S * sizeof(int32_t);
     size_t off[O_END], total = 0;
     for (int i = 0; i < O_END; ++i) {
         off[i] = total;
@@ -513,6 +527,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     unsigned long long *d_prof = (unsigned long long *)(ws + off[O_PROF]);
     SetParams *d_sp = (SetParams *)(ws + off[O_SP]);
     SetOut *d_out = (SetOut *)(ws + off[O_OUT]);
+    int32_t *d_steps = (int32_t *)(ws + off[O_STEPS]);
     for (int i = 0; i < S; ++i) hp[i].surv = d_surv + surv_off[i];
     FSGP_CUDA(cudaMemcpyAsync(d_surv, surv_all.data(), sz[O_SURV], cudaMemcpyHostToDevice, s));
     FSGP_CUDA(cudaMemcpyAsync(d_sp, hp.data(), sz[O_SP], cudaMemcpyHostToDevice, s));
@@ -532,6 +547,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
             o.per_real = x.per_real;
             o.planes = x.final_planes;
         }
+        o.steps = d_steps + i;
     }
     FSGP_CUDA(cudaMemcpyAsync(d_out, ho.data(), sz[O_OUT], cudaMemcpyHostToDevice, s));
 
@@ -641,6 +657,10 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
             ++launches;
         }
     }
+    // The launch sequence from here to the results is free of host synchronisation and
+    // host-memory copies, so it can be captured into one CUDA graph and launched at once.
+    const bool capture = opt.capture_graph != 0 && !profiling;
+    if (capture) FSGP_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     // step 0
     A.cur = buf0;
     A.nxt = buf1;
@@ -693,14 +713,29 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
         ++launches;
     }
     if (profiling) prof.stop(s);
+    if (capture) {
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        e = cudaGraphLaunch(exec, s);
+        cudaGraphExecDestroy(exec);   // freed once the launch completes
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    }
     FSGP_CUDA(cudaGetLastError());
 
-    // steps run: IC/LT report the first step whose frontier is empty in every... set of
-    // its own (read back from the per-set plane counts); SIR/SIS run all T steps
-    std::vector<unsigned long long> hpc;
-    if (want_steps && (model == FSGP_IC || model == FSGP_LT)) {
-        hpc.resize(T1 * S * 2);
-        FSGP_CUDA(cudaMemcpyAsync(hpc.data(), pc, sz[O_PC], cudaMemcpyDeviceToHost, s));
+    if (want_steps && !host_out)
+        for (int i = 0; i < S; ++i)
+            if (sets[i]->steps_run)
+                FSGP_CUDA(cudaMemcpyAsync(sets[i]->steps_run, d_steps + i, sizeof(int32_t),
+                                          cudaMemcpyDeviceToDevice, s));
+    std::vector<int32_t> hsteps;
+    if (want_steps && host_out) {
+        hsteps.resize((size_t)S);
+        FSGP_CUDA(cudaMemcpyAsync(hsteps.data(), d_steps, sz[O_STEPS], cudaMemcpyDeviceToHost, s));
     }
     if (host_out) {
         for (int i = 0; i < S; ++i) {
@@ -716,22 +751,10 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
                                           cudaMemcpyDeviceToHost, s));
         }
     }
-    if (want_steps || host_out || profiling) FSGP_CUDA(cudaStreamSynchronize(s));
-    if (want_steps) {
-        std::vector<int32_t> st((size_t)S, T);
-        for (int i = 0; i < S; ++i) {
-            if (model == FSGP_IC || model == FSGP_LT)
-                for (int k = 0; k <= T; ++k)
-                    if (hpc[((size_t)k * S + i) * 2 + 1] == 0ull) {
-                        st[i] = k;
-                        break;
-                    }
-            if (!sets[i]->steps_run) continue;
-            if (host_out) *sets[i]->steps_run = st[i];
-            else FSGP_CUDA(cudaMemcpyAsync(sets[i]->steps_run, &st[i], sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        }
-        if (!host_out) FSGP_CUDA(cudaStreamSynchronize(s));
-    }
+    if (host_out || profiling) FSGP_CUDA(cudaStreamSynchronize(s));
+    if (want_steps && host_out)
+        for (int i = 0; i < S; ++i)
+            if (sets[i]->steps_run) *sets[i]->steps_run = hsteps[i];
     if (profiling) {
         unsigned long long hb[FSGP_PROF_KINDS];
         Ctl hc;

@@ -50,13 +50,26 @@ class fsgp_options(ctypes.Structure):
                 ("hub_min_deg", ctypes.c_int32), ("hub_chunk", ctypes.c_int32),
                 ("sparse_frac", ctypes.c_double), ("r_offset", ctypes.c_int32),
                 ("t0", ctypes.c_int32), ("init_planes", ctypes.c_void_p),
-                ("profile", ctypes.POINTER(fsgp_profile)), ("reserved", ctypes.c_int32 * 8)]
+                ("profile", ctypes.POINTER(fsgp_profile)), ("capture_graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 class fsgp_result(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("counts", ctypes.c_void_p),
                 ("freq", ctypes.c_void_p), ("per_real", ctypes.c_void_p),
                 ("final_planes", ctypes.c_void_p), ("steps_run", ctypes.c_void_p)]
+
+
+class fsgp_request(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_void_p), ("model", ctypes.c_int32), ("params", fsgp_params),
+                ("seed_nodes", ctypes.c_void_p), ("n_seeds", ctypes.c_int64),
+                ("R", ctypes.c_int32), ("T", ctypes.c_int32), ("rng_seed", ctypes.c_uint64),
+                ("result", fsgp_result)]
+
+
+class fsgp_batch_options(ctypes.Structure):
+    _fields_ = [("n_streams", ctypes.c_int32), ("capture_graph", ctypes.c_int32),
+                ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
 
 
 def lib_path() -> str:
@@ -93,6 +106,13 @@ def load():
                                           ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
                                           ctypes.c_uint32, ctypes.c_uint64, P, P, P, P]
         lib.fsgp_step_noalloc.restype = ctypes.c_int
+        lib.fsgp_batch_run.argtypes = [ctypes.POINTER(fsgp_request), ctypes.c_int32,
+                                       ctypes.POINTER(fsgp_batch_options), P]
+        lib.fsgp_batch_run.restype = ctypes.c_int
+        lib.fsgp_autotune.argtypes = [P, ctypes.c_int32, ctypes.POINTER(fsgp_params), P,
+                                      ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_uint64, ctypes.POINTER(fsgp_options), P]
+        lib.fsgp_autotune.restype = ctypes.c_int
         lib.fsgp_last_error.argtypes = []
         lib.fsgp_last_error.restype = ctypes.c_char_p
         lib.fsgp_version.argtypes = []
@@ -180,6 +200,18 @@ def fsgp_step_noalloc(model, params: fsgp_params, row_ptr, col_idx, n, nnz, R, t
                                     n, nnz, R, t, ctypes.c_uint64(rng_seed), _ptr(cur_planes),
                                     _ptr(next_planes), _ptr(plane_counts),
                                     _stream_handle(stream)))
+
+
+def fsgp_batch_run(reqs, n, options: fsgp_batch_options | None = None, stream=None) -> None:
+    opt = ctypes.byref(options) if options is not None else None
+    _check(load().fsgp_batch_run(reqs, n, opt, _stream_handle(stream)))
+
+
+def fsgp_autotune(h, model, params: fsgp_params, seed_nodes, n_seeds, R, T_probe, rng_seed,
+                  options: fsgp_options, stream=None) -> None:
+    _check(load().fsgp_autotune(h, model, ctypes.byref(params), _ptr(seed_nodes), n_seeds, R,
+                                T_probe, ctypes.c_uint64(rng_seed), ctypes.byref(options),
+                                _stream_handle(stream)))
 
 
 # ----------------------------------------------------------- convenience layer
@@ -286,3 +318,42 @@ def simulate(graph: Graph, model: int, seed_sets, R: int, T: int, rng_seed: int,
     fsgp_simulate(graph.handle, model, prm, seeds, offs, n_sets, PTR_HOST, R, T, rng_seed,
                   options, res, stream)
     return out
+
+
+def batch_run(requests, *, n_streams=0, capture_graph=0, autotune=0, stream=None):
+    """Run a list of request dicts {graph: Graph, model, seeds, R, T, rng_seed, beta,
+    gamma, ic_mode, ic_p, freq: bool, per_real: bool} as one batch.  Returns one dict of
+    device result tensors per request."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = len(requests)
+    arr = (fsgp_request * max(n, 1))()
+    outs, keep = [], []
+    for i, rq in enumerate(requests):
+        g = rq["graph"]
+        seeds = np.ascontiguousarray(rq.get("seeds", np.zeros(0, np.int32)), dtype=np.int32)
+        keep.append(seeds)
+        R, T, model = int(rq["R"]), int(rq["T"]), int(rq["model"])
+        o = {"counts": torch.zeros((1, T + 1, 3), dtype=torch.int64, device=dev),
+             "steps_run": torch.zeros((1,), dtype=torch.int32, device=dev)}
+        if rq.get("freq", True):
+            o["freq"] = torch.zeros((1, 3, g.n), dtype=torch.int32, device=dev)
+        if rq.get("per_real", False):
+            o["per_real"] = torch.zeros((1, R, T + 1, 3), dtype=torch.int32, device=dev)
+        outs.append(o)
+        q = arr[i]
+        q.graph = g.handle
+        q.model = model
+        q.params = fsgp_params(beta=rq.get("beta", 0.0), gamma=rq.get("gamma", 0.0),
+                               ic_mode=rq.get("ic_mode", IC_WEIGHTED_CASCADE), ic_p=rq.get("ic_p", 0.0))
+        q.seed_nodes = seeds.ctypes.data if seeds.size else None
+        q.n_seeds = int(seeds.size)
+        q.R, q.T, q.rng_seed = R, T, int(rq["rng_seed"])
+        q.result.flags = PTR_DEVICE
+        q.result.counts = _ptr(o["counts"])
+        q.result.freq = _ptr(o.get("freq"))
+        q.result.per_real = _ptr(o.get("per_real"))
+        q.result.steps_run = _ptr(o["steps_run"])
+    bo = fsgp_batch_options(n_streams=n_streams, capture_graph=capture_graph, autotune=autotune)
+    fsgp_batch_run(arr, n, bo, stream)
+    return outs

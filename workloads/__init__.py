@@ -210,3 +210,47 @@ def rmat26(model: int, g: Graph | None = None, scale: int = 26) -> Workload:
     nm = "sir" if model == SIR else "sis"
     return Workload(f"rmat{scale}_{nm}_R256_T100", g, model, beta=0.01, gamma=0.05,
                     seed_sets=[seeds], R=256, T=100, rng_seed=3)
+
+
+# ------------------------------------------------------------- batched requests
+
+@dataclass
+class BatchRequest:
+    graph_index: int
+    model: int
+    seeds: np.ndarray
+    R: int
+    T: int
+    beta: float
+    gamma: float
+    rng_seed: int
+
+
+def batch_pool(n_graphs: int = 64, n_requests: int = 4096, n_min: int = 1_000,
+               n_max: int = 2_000_000, seed: int = 12345 + 4, T: int = 100):
+    """Pool of power-law (BA, m in 2..8) and ER graphs with n log-uniform in
+    [n_min, n_max], and requests with model uniform over SIR/SIS/IC/LT, R in
+    {32, ..., 1024}, seed-set size uniform in 1..500, beta ~ U[0.005, 0.2], gamma = 0.1,
+    IC weighted cascade, T steps (IC/LT stop earlier at quiescence)."""
+    graphs = []
+    lo, hi = np.log(n_min), np.log(n_max)
+    for i in range(n_graphs):
+        n = int(round(np.exp(lo + (hi - lo) * uniform01(seed, 1, i))))
+        if hash64(seed, 2, i) % 4 == 0:
+            deg = 4 + int(hash64(seed, 3, i) % 13)
+            graphs.append(er(n, float(deg), seed=seed * 1000 + i))
+        else:
+            m = 2 + int(hash64(seed, 4, i) % 7)
+            graphs.append(ba(max(n, m + 2), m, seed=seed * 1000 + i))
+    Rs = [32, 64, 128, 256, 512, 1024]
+    reqs = []
+    for j in range(n_requests):
+        gi = int(hash64(seed, 5, j) % n_graphs)
+        g = graphs[gi]
+        k = 1 + int(hash64(seed, 6, j) % 500)
+        reqs.append(BatchRequest(
+            graph_index=gi, model=int(hash64(seed, 7, j) % 4),
+            seeds=seed_set(g.n, min(k, g.n), seed=seed * 100000 + j),
+            R=Rs[int(hash64(seed, 8, j) % len(Rs))], T=T,
+            beta=0.005 + 0.195 * uniform01(seed, 9, j), gamma=0.1, rng_seed=1 + j))
+    return graphs, reqs
