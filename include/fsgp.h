@@ -222,6 +222,47 @@ int fsgp_autotune(const fsgp_graph *g, int32_t model, const fsgp_params *params,
                   const int32_t *seed_nodes, int64_t n_seeds, int32_t R, int32_t T_probe,
                   uint64_t rng_seed, fsgp_options *inout, void *stream);
 
+/* ------------------------------------------------------------ learned surrogate
+ * The paper has no learned component.  This 3-layer message-passing network predicts
+ * each node's probability of being infected by the end of a run from the seed set and
+ * (beta, gamma), to screen many candidate seed sets before Monte Carlo re-scores the
+ * best; plain Monte Carlo (fsgp_simulate) stays the judge.
+ *   x_v = [seed_v, beta, gamma, log(1+d_in), log(1+d_out), log(1+k_v), 0, 0], k_v = in-arcs
+ *         of v from seeds
+ *   h'_v = ReLU(h_v Ws_l + mean_{u->v} h_u Wn_l + b_l), l = 1..3, width 64
+ *   p_v = sigmoid(h3_v . w_o + b_o);  loss = mean_v (p_v - y_v)^2
+ * Dense products run on the tensor cores with bfloat16 operands and float32 accumulation;
+ * training keeps float32 master weights and Adam state.  Parameters are one float32
+ * vector: Ws1[8x64] Wn1[8x64] b1[64] Ws2[64x64] Wn2[64x64] b2 Ws3 Wn3 b3 wo[64] bo[1]
+ * (row-major, rows = input features). */
+typedef struct fsgp_surrogate fsgp_surrogate;
+
+int fsgp_surrogate_num_params(void);
+/* He-normal weights from a SplitMix64 stream seeded by init_seed, zero biases. */
+int fsgp_surrogate_create(uint64_t init_seed, fsgp_surrogate **out);
+int fsgp_surrogate_destroy(fsgp_surrogate *s);
+/* Copy the float32 parameters out (get_host) and/or in (set_host; resets Adam). */
+int fsgp_surrogate_params(fsgp_surrogate *s, float *get_host, const float *set_host);
+/* Per-node probabilities p_out (device, n floats) for one seed set (host array). */
+int fsgp_surrogate_forward(fsgp_surrogate *s, const fsgp_graph *g, const int32_t *seeds_host,
+                           int64_t n_seeds, double beta, double gamma, float *p_out, void *stream);
+/* Loss and gradient for targets y (device, n floats); outputs are host pointers (either
+ * may be NULL).  Synchronises the stream. */
+int fsgp_surrogate_grad(fsgp_surrogate *s, const fsgp_graph *g, const int32_t *seeds_host,
+                        int64_t n_seeds, double beta, double gamma, const float *y,
+                        double *loss_out, float *grad_out, void *stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on one sample;
+ * loss_out (host, may be NULL) receives the loss before the step. */
+int fsgp_surrogate_train_step(fsgp_surrogate *s, const fsgp_graph *g, const int32_t *seeds_host,
+                              int64_t n_seeds, double beta, double gamma, const float *y,
+                              float lr, double *loss_out, void *stream);
+/* Scores (sum over nodes of p) of n_cand candidate seed sets of k nodes each
+ * (cand_host[n_cand][k]) into scores_out (host, n_cand floats).  One CUDA graph per call
+ * is replayed once per candidate.  Synchronises the stream. */
+int fsgp_surrogate_screen(fsgp_surrogate *s, const fsgp_graph *g, const int32_t *cand_host,
+                          int32_t k, int32_t n_cand, double beta, double gamma, float *scores_out,
+                          void *stream);
+
 /* One synchronous step (Eq. nodestate) of `model` that allocates no device memory.
  * The paper has no counterpart: this entry point exists for callers that cannot call
  * cudaMalloc -- code running inside a stream capture or a pre-built CUDA graph, a

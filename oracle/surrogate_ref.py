@@ -3,7 +3,8 @@
 The paper has no learned component; this network is the project's screening surrogate.
 Definition (restated here, computed in float64):
 
-  x_v   = [seed_v, beta, gamma, log(1+d_in(v)), log(1+d_out(v)), 0, 0, 0]       (8)
+  x_v   = [seed_v, beta, gamma, log(1+d_in(v)), log(1+d_out(v)), log(1+k_v), 0, 0]   (8)
+          k_v = number of in-arcs of v whose source is a seed (with multiplicity)
   m_v   = mean over in-arcs u -> v of h_u (0 when d_in(v) = 0; arcs with multiplicity)
   h'_v  = ReLU(h_v Ws_l + m_v Wn_l + b_l),  l = 1, 2, 3, width 64
   p_v   = sigmoid(h3_v . w_o + b_o)
@@ -64,6 +65,11 @@ def features(row_ptr, col_idx, seeds, beta, gamma):
     x[:, 2] = gamma
     x[:, 3] = np.log1p(d_in)
     x[:, 4] = np.log1p(d_out)
+    is_seed = np.zeros(n, dtype=bool)
+    is_seed[np.asarray(seeds, dtype=np.int64)] = True
+    dst = np.repeat(np.arange(n), d_in)
+    k = np.bincount(dst[is_seed[np.asarray(col_idx, dtype=np.int64)]], minlength=n)
+    x[:, 5] = np.log1p(k)
     return x
 
 

@@ -659,7 +659,9 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     }
     // The launch sequence from here to the results is free of host synchronisation and
     // host-memory copies, so it can be captured into one CUDA graph and launched at once.
-    const bool capture = opt.capture_graph != 0 && !profiling;
+    // (the legacy default stream cannot be captured; such callers launch directly)
+    const bool capture = opt.capture_graph != 0 && !profiling && s != nullptr && s != cudaStreamLegacy &&
+                         s != cudaStreamPerThread;
     if (capture) FSGP_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     // step 0
     A.cur = buf0;

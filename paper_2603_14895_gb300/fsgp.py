@@ -113,6 +113,26 @@ def load():
                                       ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_uint64, ctypes.POINTER(fsgp_options), P]
         lib.fsgp_autotune.restype = ctypes.c_int
+        lib.fsgp_surrogate_num_params.argtypes = []
+        lib.fsgp_surrogate_num_params.restype = ctypes.c_int
+        lib.fsgp_surrogate_create.argtypes = [ctypes.c_uint64, ctypes.POINTER(P)]
+        lib.fsgp_surrogate_create.restype = ctypes.c_int
+        lib.fsgp_surrogate_destroy.argtypes = [P]
+        lib.fsgp_surrogate_destroy.restype = ctypes.c_int
+        lib.fsgp_surrogate_params.argtypes = [P, P, P]
+        lib.fsgp_surrogate_params.restype = ctypes.c_int
+        lib.fsgp_surrogate_forward.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_double,
+                                               ctypes.c_double, P, P]
+        lib.fsgp_surrogate_forward.restype = ctypes.c_int
+        lib.fsgp_surrogate_grad.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_double,
+                                            ctypes.c_double, P, P, P, P]
+        lib.fsgp_surrogate_grad.restype = ctypes.c_int
+        lib.fsgp_surrogate_train_step.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_double,
+                                                  ctypes.c_double, P, ctypes.c_float, P, P]
+        lib.fsgp_surrogate_train_step.restype = ctypes.c_int
+        lib.fsgp_surrogate_screen.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_double, ctypes.c_double, P, P]
+        lib.fsgp_surrogate_screen.restype = ctypes.c_int
         lib.fsgp_last_error.argtypes = []
         lib.fsgp_last_error.restype = ctypes.c_char_p
         lib.fsgp_version.argtypes = []
@@ -357,3 +377,73 @@ def batch_run(requests, *, n_streams=0, capture_graph=0, autotune=0, stream=None
     bo = fsgp_batch_options(n_streams=n_streams, capture_graph=capture_graph, autotune=autotune)
     fsgp_batch_run(arr, n, bo, stream)
     return outs
+
+
+class Surrogate:
+    """Owns an fsgp_surrogate handle (thin wrapper over the fsgp_surrogate_* calls)."""
+
+    def __init__(self, init_seed: int = 0):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.fsgp_surrogate_create(ctypes.c_uint64(init_seed), ctypes.byref(h)))
+        self.handle = h
+        self.n_params = lib.fsgp_surrogate_num_params()
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().fsgp_surrogate_params(self.handle, out.ctypes.data, None))
+        return out
+
+    def set_params(self, theta) -> None:
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        assert t.size == self.n_params
+        _check(load().fsgp_surrogate_params(self.handle, None, t.ctypes.data))
+
+    def forward(self, graph, seeds, beta, gamma, stream=None):
+        import torch
+        seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+        p = torch.empty(graph.n, dtype=torch.float32, device="cuda")
+        _check(load().fsgp_surrogate_forward(self.handle, graph.handle,
+                                             seeds.ctypes.data if seeds.size else None,
+                                             seeds.size, beta, gamma, _ptr(p),
+                                             _stream_handle(stream)))
+        return p
+
+    def grad(self, graph, seeds, beta, gamma, y, stream=None):
+        seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+        loss = ctypes.c_double(0.0)
+        g = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().fsgp_surrogate_grad(self.handle, graph.handle,
+                                          seeds.ctypes.data if seeds.size else None, seeds.size,
+                                          beta, gamma, _ptr(y), ctypes.byref(loss), g.ctypes.data,
+                                          _stream_handle(stream)))
+        return loss.value, g
+
+    def train_step(self, graph, seeds, beta, gamma, y, lr=1e-3, stream=None):
+        seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+        loss = ctypes.c_double(0.0)
+        _check(load().fsgp_surrogate_train_step(self.handle, graph.handle,
+                                                seeds.ctypes.data if seeds.size else None,
+                                                seeds.size, beta, gamma, _ptr(y),
+                                                ctypes.c_float(lr), ctypes.byref(loss),
+                                                _stream_handle(stream)))
+        return loss.value
+
+    def screen(self, graph, candidates, beta, gamma, stream=None) -> np.ndarray:
+        c = np.ascontiguousarray(candidates, dtype=np.int32)
+        n_cand, k = c.shape
+        out = np.zeros(n_cand, dtype=np.float32)
+        _check(load().fsgp_surrogate_screen(self.handle, graph.handle, c.ctypes.data, k, n_cand,
+                                            beta, gamma, out.ctypes.data, _stream_handle(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            load().fsgp_surrogate_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

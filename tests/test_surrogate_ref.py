@@ -53,6 +53,22 @@ def test_closed_forms():
     assert abs(lhs - rhs) < 1e-9 * abs(lhs)
 
 
+def test_seed_in_arc_feature_brute_force():
+    """Feature 5 is log(1 + number of in-arcs from seeds), counted arc by arc."""
+    g = W.from_arcs(5, [0, 0, 1, 2, 3, 0, 4], [1, 1, 2, 1, 4, 3, 0])
+    seeds = np.array([0, 2], dtype=np.int32)
+    x = S.features(g.row_ptr, g.col_idx, seeds, 0.1, 0.2)
+    want = np.zeros(5)
+    for u, v in zip([0, 0, 1, 2, 3, 0, 4], [1, 1, 2, 1, 4, 3, 0]):
+        if u in (0, 2):
+            want[v] += 1
+    assert np.array_equal(want, [0, 3, 0, 1, 0])
+    assert np.allclose(x[:, 5], np.log1p(want))
+    assert np.array_equal(x[:, 0], [1, 0, 1, 0, 0])
+    assert np.allclose(x[:, 3], np.log1p([1, 3, 1, 1, 1]))   # in-degrees
+    assert np.allclose(x[:, 4], np.log1p([3, 1, 1, 1, 1]))   # out-degrees
+
+
 def test_bf16_rounding():
     vals = np.array([1.0, 1.00390625, 1.001953125, 1.005859375, -2.5, 3.0e-3, 65504.0,
                      1.01171875])
