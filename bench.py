@@ -274,6 +274,187 @@ def run_batch_bench(args):
             "clocks": clocks}
 
 
+# -------------------------------------------------------------- learned surrogate
+
+SG_R, SG_T, SG_GAMMA, SG_K = 1024, 100, 0.1, 20
+
+
+def _sg_forward_bytes(n: int, nnz: int) -> float:
+    """Compulsory bytes of one surrogate forward: every array read or written once
+    (row pointers 4 B/node, column indices 4 B/arc, bfloat16 activations 2 B/value):
+    layer 1 aggregate 36 n + 4 nnz, layer 1 dense 160 n, layers 2-3 aggregate
+    260 n + 4 nnz each, layers 2-3 dense 384 n each, head 128 n."""
+    return 1612.0 * n + 12.0 * nnz
+
+
+def run_surrogate_bench(args):
+    """Learned surrogate, end to end: graphs, Monte Carlo targets, training, held-out
+    error, screening, Monte Carlo re-scoring.
+
+    Graphs: args.sg_graphs synthetic BA / R-MAT graphs with n = 100k .. 1M; the first 80%
+    train, the rest are held out.  Targets: per node, the fraction of R = 1024 SIR
+    realizations (T = 100, gamma = 0.1) in which it was ever infected, for 8 random
+    20-node seed sets per graph with beta ~ U[0.01, 0.1].  Error: mean absolute error of
+    the predicted probabilities against those frequencies on the held-out graphs.
+    Screening: 10,000 candidate 20-node sets per screened graph; the surrogate's top 100
+    and 100 random candidates are re-scored by Monte Carlo (R = 1024, T = 100)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2603_14895_gb300 import fsgp
+    torch.cuda.set_device(0)
+    NG = args.sg_graphs
+    n_train = max(1, int(round(0.8 * NG)))
+    t0 = time.time()
+    graphs = W.surrogate_pool(NG)
+    log(f"[surrogate] {NG} graphs, {sum(g.n for g in graphs)} nodes, "
+        f"{sum(g.nnz for g in graphs)} arcs in {time.time() - t0:.1f}s")
+    gobjs = [fsgp.Graph(g.row_ptr, g.col_idx) for g in graphs]
+    sets = [W.surrogate_sets(g, i) for i, g in enumerate(graphs)]
+
+    # Monte Carlo targets, batched over requests, a slice of graphs at a time
+    t0 = time.time()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    targets = [[None] * len(sets[i]) for i in range(NG)]
+    mc_ms = 0.0
+    for c0 in range(0, NG, 20):
+        spec, where = [], []
+        for gi in range(c0, min(NG, c0 + 20)):
+            for j, (sd, beta) in enumerate(sets[gi]):
+                spec.append(dict(graph=gobjs[gi], model=0, seeds=sd, R=SG_R, T=SG_T,
+                                 rng_seed=1000 * gi + j + 1, beta=beta, gamma=SG_GAMMA, freq=True))
+                where.append((gi, j))
+        ev0.record()
+        outs = fsgp.batch_run(spec, capture_graph=1)
+        ev1.record()
+        torch.cuda.synchronize()
+        mc_ms += ev0.elapsed_time(ev1)
+        for (gi, j), o in zip(where, outs):
+            fr = o["freq"][0]
+            targets[gi][j] = ((fr[1] + fr[2]).float() / SG_R).contiguous()
+        del outs
+        for gi in range(c0, min(NG, c0 + 20)):
+            gobjs[gi].trim()
+    mc_units = sum(float(graphs[gi].nnz) * SG_R * SG_T * len(sets[gi]) for gi in range(NG))
+    log(f"[surrogate] targets: {sum(len(s) for s in sets)} runs, {mc_ms / 1e3:.1f}s on device, "
+        f"{time.time() - t0:.1f}s wall")
+
+    # training
+    sg = fsgp.Surrogate(args.sg_seed)
+    samples = [(gi, j) for gi in range(n_train) for j in range(len(sets[gi]))]
+    rng = np.random.default_rng(args.sg_seed)
+    E = args.sg_epochs
+    total = E * len(samples)
+    it = 0
+    t0 = time.time()
+    ev0.record()
+    for ep in range(E):
+        for idx in rng.permutation(len(samples)):
+            gi, j = samples[idx]
+            lr = args.sg_lr * (0.05 + 0.95 * 0.5 * (1 + np.cos(np.pi * it / total)))
+            sd, beta = sets[gi][j]
+            sg.train_step(gobjs[gi], sd, beta, SG_GAMMA, targets[gi][j], lr=float(lr), want_loss=False)
+            it += 1
+    ev1.record()
+    torch.cuda.synchronize()
+    train_ms = ev0.elapsed_time(ev1)
+    train_nodes = sum(graphs[gi].n for gi, _ in samples) * E
+    log(f"[surrogate] {E} epochs x {len(samples)} samples in {train_ms / 1e3:.1f}s")
+
+    def mae_over(gis):
+        err = nodes = 0.0
+        const_err = 0.0
+        rel = []
+        ybar = float(np.mean([float(targets[g][j].mean()) for g in range(n_train) for j in range(len(sets[g]))]))
+        for gi in gis:
+            for j, (sd, beta) in enumerate(sets[gi]):
+                p = sg.forward(gobjs[gi], sd, beta, SG_GAMMA)
+                y = targets[gi][j]
+                err += float((p - y).abs().sum())
+                const_err += float((y - ybar).abs().sum())
+                nodes += y.numel()
+                ys, ps = float(y.sum()), float(p.sum())
+                rel.append(abs(ps - ys) / max(ys, 1.0))
+        return err / nodes, const_err / nodes, float(np.median(rel)), float(np.mean(rel))
+
+    held = list(range(n_train, NG))
+    mae_train, _, _, _ = mae_over(range(min(n_train, 8)))
+    mae, mae_const, spread_rel_med, spread_rel_mean = mae_over(held)
+    log(f"[surrogate] held-out MAE {mae:.4f} (constant predictor {mae_const:.4f}); "
+        f"train MAE {mae_train:.4f}; spread rel. error median {spread_rel_med:.3f}")
+
+    # screening on held-out graphs
+    sampler = ClockSampler(gpu_selector(torch))
+    sampler.start()
+    screen = []
+    scr_ms = mc_cand_ms = 0.0
+    scr_bytes = 0.0
+    n_scr = 0
+    for gi in held[:args.sg_screen_graphs]:
+        g = graphs[gi]
+        beta = args.sg_beta_screen
+        cands = W.surrogate_candidates(g, args.sg_cands, SG_K, seed=7000 + gi)
+        sg.screen(gobjs[gi], cands[:64], beta, SG_GAMMA)     # warm-up (graph capture, buffers)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        scores = sg.screen(gobjs[gi], cands, beta, SG_GAMMA)
+        dt = (time.perf_counter() - t1) * 1e3
+        scr_ms += dt
+        scr_bytes += _sg_forward_bytes(g.n, g.nnz) * len(cands)
+        n_scr += len(cands)
+        top = np.argsort(-scores)[:100]
+        rnd = np.random.default_rng(gi).choice(len(cands), 100, replace=False)
+        pick = np.concatenate([top, rnd])
+        ev0.record()
+        out = fsgp.simulate(gobjs[gi], 0, [cands[c] for c in pick], SG_R, SG_T, 77 + gi,
+                            beta=beta, gamma=SG_GAMMA, freq=False, steps_run=False)
+        ev1.record()
+        torch.cuda.synchronize()
+        gobjs[gi].trim()
+        mc_cand_ms += ev0.elapsed_time(ev1)
+        cnt = out["counts"].cpu().numpy()
+        spread = (cnt[:, SG_T, 1] + cnt[:, SG_T, 2]) / SG_R
+        st, sr = spread[:100], spread[100:]
+        rs = np.argsort(np.argsort(scores[rnd]))
+        rm = np.argsort(np.argsort(sr))
+        screen.append({"graph": gi, "n": g.n, "nnz": g.nnz,
+                       "top100_mc_mean": float(st.mean()), "random100_mc_mean": float(sr.mean()),
+                       "top100_mc_best": float(st.max()), "random100_mc_best": float(sr.max()),
+                       "spearman_random100": float(np.corrcoef(rs, rm)[0, 1]),
+                       "screen_ms": dt})
+        log(f"[surrogate] graph {gi} n={g.n}: screen {len(cands)} in {dt:.0f} ms; top-100 MC "
+            f"{st.mean():.1f} vs random-100 {sr.mean():.1f}; spearman {screen[-1]['spearman_random100']:.2f}")
+    clocks = sampler.stop()
+    mc_per_cand_ms = mc_cand_ms / (200.0 * len(screen))
+    sg_per_cand_ms = scr_ms / n_scr
+    achieved = scr_bytes / (scr_ms / 1e3) / 1e9
+    peak, peak_src = measured_peaks()
+    return {"metric": "surrogate-screened seed sets/sec", "value": n_scr / (scr_ms / 1e3),
+            "unit": "seed sets/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": scr_ms / max(1, len(screen)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"surrogate_{NG}graphs_{args.sg_cands}cands",
+                       "graphs": "BA m=2..6 n=100k..1M and R-MAT scale 17..19 ef 8",
+                       "train_graphs": n_train, "held_out_graphs": NG - n_train,
+                       "sets_per_graph": 8, "seed_set_size": SG_K, "R": SG_R, "T": SG_T,
+                       "beta_train": "U[0.01,0.1]", "beta_screen": args.sg_beta_screen, "gamma": SG_GAMMA,
+                       "epochs": E, "lr": args.sg_lr,
+                       "l2": "graphs of this size keep activations partly L2-resident"},
+            "mae_vs_mc_R1024": mae, "mae_constant_predictor": mae_const, "mae_train_subset": mae_train,
+            "spread_rel_err_median": spread_rel_med, "spread_rel_err_mean": spread_rel_mean,
+            "mc_ms_per_candidate": mc_per_cand_ms, "surrogate_ms_per_candidate": sg_per_cand_ms,
+            "screening_speedup": mc_per_cand_ms / sg_per_cand_ms,
+            "screen": screen,
+            "targets_mc": {"runs": sum(len(s) for s in sets), "device_s": mc_ms / 1e3,
+                           "edge_realization_steps_per_s": mc_units / (mc_ms / 1e3)},
+            "train": {"steps": total, "device_s": train_ms / 1e3,
+                      "node_samples_per_s": train_nodes / (train_ms / 1e3)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if peak else None, "traffic": None,
+                         "note": "whole screening forward, compulsory bytes; peak " + peak_src},
+            "clocks": clocks}
+
+
 # ------------------------------------------------------------------------- main
 
 def main():
@@ -286,7 +467,14 @@ def main():
     ap.add_argument("--scale", type=int, default=SCALE)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="rmat26", choices=["rmat26", "batch"])
+    ap.add_argument("--workload", default="rmat26", choices=["rmat26", "batch", "surrogate"])
+    ap.add_argument("--sg-graphs", type=int, default=200)
+    ap.add_argument("--sg-epochs", type=int, default=6)
+    ap.add_argument("--sg-lr", type=float, default=2e-3)
+    ap.add_argument("--sg-seed", type=int, default=1)
+    ap.add_argument("--sg-cands", type=int, default=10_000)
+    ap.add_argument("--sg-screen-graphs", type=int, default=4)
+    ap.add_argument("--sg-beta-screen", type=float, default=0.01)
     ap.add_argument("--batch-graphs", type=int, default=64)
     ap.add_argument("--batch-requests", type=int, default=4096)
     args = ap.parse_args()
@@ -298,6 +486,9 @@ def main():
 
     if args.workload == "batch" and args.impl == "fsgp":
         print(json.dumps(run_batch_bench(args)), flush=True)
+        return
+    if args.workload == "surrogate" and args.impl == "fsgp":
+        print(json.dumps(run_surrogate_bench(args)), flush=True)
         return
 
     if args.impl == "reference":

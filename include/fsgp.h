@@ -157,6 +157,12 @@ int fsgp_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t n,
 /* Release a graph and its workspace (NULL is accepted).  Synchronises the device. */
 int fsgp_graph_destroy(fsgp_graph *g);
 
+/* Free the graph's cached simulation workspace (state planes, lists, counters), which
+ * fsgp_simulate / fsgp_batch_run keep between calls and grow to the largest run seen;
+ * the next run allocates it again.  Useful when many graphs stay alive.  Synchronises
+ * the device.  Errors: EINVAL (NULL), ECUDA. */
+int fsgp_graph_trim(fsgp_graph *g);
+
 /* Query sizes: any output pointer may be NULL. */
 int fsgp_graph_info(const fsgp_graph *g, int32_t *n, int64_t *nnz, int32_t *max_in_degree,
                     int64_t *device_bytes);
@@ -228,7 +234,7 @@ int fsgp_autotune(const fsgp_graph *g, int32_t model, const fsgp_params *params,
  * (beta, gamma), to screen many candidate seed sets before Monte Carlo re-scores the
  * best; plain Monte Carlo (fsgp_simulate) stays the judge.
  *   x_v = [seed_v, beta, gamma, log(1+d_in), log(1+d_out), log(1+k_v), 0, 0], k_v = in-arcs
- *         of v from seeds
+ *         of v from seeds (a seed listed twice counts twice)
  *   h'_v = ReLU(h_v Ws_l + mean_{u->v} h_u Wn_l + b_l), l = 1..3, width 64
  *   p_v = sigmoid(h3_v . w_o + b_o);  loss = mean_v (p_v - y_v)^2
  * Dense products run on the tensor cores with bfloat16 operands and float32 accumulation;

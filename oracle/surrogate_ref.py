@@ -4,18 +4,20 @@ The paper has no learned component; this network is the project's screening surr
 Definition (restated here, computed in float64):
 
   x_v   = [seed_v, beta, gamma, log(1+d_in(v)), log(1+d_out(v)), log(1+k_v), 0, 0]   (8)
-          k_v = number of in-arcs of v whose source is a seed (with multiplicity)
+          k_v = number of in-arcs of v whose source is a seed (arcs and seeds both
+                counted with multiplicity: a seed listed twice counts twice)
   m_v   = mean over in-arcs u -> v of h_u (0 when d_in(v) = 0; arcs with multiplicity)
   h'_v  = ReLU(h_v Ws_l + m_v Wn_l + b_l),  l = 1, 2, 3, width 64
   p_v   = sigmoid(h3_v . w_o + b_o)
   loss  = mean_v (p_v - y_v)^2,  y_v = fraction of realizations in which v was infected
 
 The GPU feeds its tensor-core products with bfloat16 operands (weights, inputs,
-activations, aggregated means) and accumulates in float32.  With `bf16=True` this
-reference rounds exactly those operands to bfloat16 (round to nearest even) and keeps
-everything else in float64, so the two differ only by float32 accumulation order.  With
-`bf16=False` it is the plain float64 function, whose analytic gradients the tests check
-against finite differences.
+activations, aggregated means, and in the backward pass the pre-activation gradients dz)
+and accumulates in float32.  With `bf16=True` this reference rounds exactly those
+operands to bfloat16 (round to nearest even) and keeps everything else in float64 (the
+bias gradient sums the unrounded dz), so the two differ only by float32 accumulation
+order.  With `bf16=False` it is the plain float64 function, whose analytic gradients the
+tests check against finite differences.
 """
 from __future__ import annotations
 
@@ -65,10 +67,9 @@ def features(row_ptr, col_idx, seeds, beta, gamma):
     x[:, 2] = gamma
     x[:, 3] = np.log1p(d_in)
     x[:, 4] = np.log1p(d_out)
-    is_seed = np.zeros(n, dtype=bool)
-    is_seed[np.asarray(seeds, dtype=np.int64)] = True
+    times_seed = np.bincount(np.asarray(seeds, dtype=np.int64), minlength=n)
     dst = np.repeat(np.arange(n), d_in)
-    k = np.bincount(dst[is_seed[np.asarray(col_idx, dtype=np.int64)]], minlength=n)
+    k = np.bincount(dst, weights=times_seed[np.asarray(col_idx, dtype=np.int64)], minlength=n)
     x[:, 5] = np.log1p(k)
     return x
 
@@ -115,7 +116,8 @@ def forward(theta, row_ptr, col_idx, x, bf16=True):
 def loss_and_grad(theta, row_ptr, col_idx, x, y, bf16=True):
     """MSE loss and its gradient w.r.t. the flat parameters (operands rounded as on the
     GPU when bf16=True; the gradient is that of the rounded forward with the rounding
-    treated as identity, i.e. straight through, as the GPU computes it)."""
+    treated as identity, i.e. straight through, as the GPU computes it, with dz rounded
+    where it enters a product)."""
     P = unflatten(theta)
     r = bf16_round if bf16 else (lambda a: np.asarray(a, dtype=np.float64))
     n = len(row_ptr) - 1
@@ -130,11 +132,12 @@ def loss_and_grad(theta, row_ptr, col_idx, x, y, bf16=True):
         h, m, z = cache[l - 1]
         Ws, Wn = r(P[f"Ws{l}"]), r(P[f"Wn{l}"])
         dz = dh * (z > 0)
-        G[f"Ws{l}"] = h.T @ dz
-        G[f"Wn{l}"] = m.T @ dz
+        dzr = r(dz)
+        G[f"Ws{l}"] = h.T @ dzr
+        G[f"Wn{l}"] = m.T @ dzr
         G[f"b{l}"] = dz.sum(axis=0)
-        dm = dz @ Wn.T
-        dh = dz @ Ws.T + _mean_agg_T(row_ptr, col_idx, dm)
+        dm = dzr @ Wn.T
+        dh = dzr @ Ws.T + _mean_agg_T(row_ptr, col_idx, dm)
     return loss, flatten(G)
 
 

@@ -94,6 +94,25 @@ struct Workspace {
     size_t bytes = 0;
 };
 
+// Per-graph tables of the learned surrogate's aggregation, built on first use: rows with
+// at least kSgLong arcs are split into chunks of kSgChunk arcs whose partial sums meet
+// in a float32 accumulator (zero between uses).
+constexpr int32_t kSgLong = 256;
+constexpr int32_t kSgChunk = 256;
+struct SgCache {
+    int built = 0;
+    float *inv_din = nullptr;     // [n] 1 / d_in (0 when d_in = 0)
+    int4 *in_items = nullptr;     // chunks of long in-CSR rows: {row, begin, end, slot}
+    int32_t n_in_items = 0;
+    int32_t *in_long = nullptr;   // [n_in_long] the long in-CSR rows, by slot
+    int32_t n_in_long = 0;
+    int4 *out_items = nullptr;    // chunks of long out-CSR rows
+    int32_t n_out_items = 0;
+    int32_t *out_long = nullptr;
+    int32_t n_out_long = 0;
+    float *acc = nullptr;         // [max(n_in_long, n_out_long)][64]
+};
+
 }  // namespace fsgp
 
 struct fsgp_graph {
@@ -110,6 +129,7 @@ struct fsgp_graph {
     fsgp::ClassInfo cls{};
     fsgp::HubTable hub{};
     fsgp::Workspace ws{};
+    fsgp::SgCache sgc{};
     int sm_count = 0;
     size_t device_bytes = 0;
 };

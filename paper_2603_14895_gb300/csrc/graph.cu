@@ -256,6 +256,12 @@ static void release(fsgp_graph *g) {
     cudaFree(g->rows_sorted);
     cudaFree(g->hub.d_chunk_base);
     cudaFree(g->ws.ptr);
+    cudaFree(g->sgc.inv_din);
+    cudaFree(g->sgc.in_items);
+    cudaFree(g->sgc.in_long);
+    cudaFree(g->sgc.out_items);
+    cudaFree(g->sgc.out_long);
+    cudaFree(g->sgc.acc);
     delete g;
 }
 
@@ -441,6 +447,22 @@ extern "C" int fsgp_graph_destroy(fsgp_graph *g) {
     release(g);
     cudaSetDevice(dev);
     return FSGP_OK;
+}
+
+extern "C" int fsgp_graph_trim(fsgp_graph *g) {
+    set_error("");
+    if (!g) return fail(FSGP_EINVAL, "graph is NULL");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaSetDevice(g->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && g->ws.ptr) e = cudaFree(g->ws.ptr);
+    if (e == cudaSuccess) {
+        g->ws.ptr = nullptr;
+        g->ws.bytes = 0;
+    }
+    cudaSetDevice(dev);
+    return e == cudaSuccess ? FSGP_OK : cuda_fail(e, "fsgp_graph_trim");
 }
 
 extern "C" int fsgp_graph_info(const fsgp_graph *g, int32_t *n, int64_t *nnz,

@@ -63,15 +63,15 @@ __global__ void k_features(const int32_t *__restrict__ row_ptr, const int32_t *_
 }
 
 // Seed in-arc counts: for every out-arc s -> v of the seeds of candidate *cur add `delta`
-// to cnt[v] (one warp per seed).
+// to cnt[v] (one CTA per seed, so hub seeds spread over the CTA's threads).
 __global__ void k_seed_count(const int32_t *__restrict__ cand, int32_t k, const int32_t *cur,
                              const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ out_dst,
                              int32_t delta, int32_t *cnt) {
     const int c = *cur;
-    const int lane = threadIdx.x & 31;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < k; i += (gridDim.x * blockDim.x) >> 5) {
+    for (int i = blockIdx.x; i < k; i += gridDim.x) {
         const int32_t sd = cand[(size_t)c * k + i];
-        for (int32_t a = out_ptr[sd] + lane; a < out_ptr[sd + 1]; a += 32) atomicAdd(&cnt[out_dst[a]], delta);
+        for (int32_t a = out_ptr[sd] + threadIdx.x; a < out_ptr[sd + 1]; a += blockDim.x)
+            atomicAdd(&cnt[out_dst[a]], delta);
     }
 }
 
@@ -80,10 +80,9 @@ __global__ void k_seed_feat(const int32_t *__restrict__ cand, int32_t k, const i
                             const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ out_dst,
                             const int32_t *__restrict__ cnt, bf16 *x) {
     const int c = *cur;
-    const int lane = threadIdx.x & 31;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < k; i += (gridDim.x * blockDim.x) >> 5) {
+    for (int i = blockIdx.x; i < k; i += gridDim.x) {
         const int32_t sd = cand[(size_t)c * k + i];
-        for (int32_t a = out_ptr[sd] + lane; a < out_ptr[sd + 1]; a += 32) {
+        for (int32_t a = out_ptr[sd] + threadIdx.x; a < out_ptr[sd + 1]; a += blockDim.x) {
             const int32_t v = out_dst[a];
             x[(size_t)v * F0 + 5] = __float2bfloat16(log1pf((float)cnt[v]));
         }
@@ -101,24 +100,59 @@ __global__ void k_seed_bits(const int32_t *__restrict__ cand, int32_t k, int32_t
 }
 
 // m_v = mean over in-arcs of h_u (bfloat16 in and out, float32 sums).  F/2 threads per
-// row, one bfloat16 pair each.
+// work item, one bfloat16 pair each.  Items 0..n-1 are rows (rows with >= kSgLong arcs
+// are skipped); items n.. are the chunks of those long rows, whose partial sums go to
+// acc[slot] for k_agg_fin.
 template <int F>
 __global__ void k_agg(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int32_t n,
-                      const bf16 *__restrict__ h, bf16 *m) {
+                      const bf16 *__restrict__ h, bf16 *m, const int4 *__restrict__ items, int32_t n_items,
+                      float *acc) {
     constexpr int TPR = F / 2;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int j = (int)(t % TPR);
-    for (int64_t v = t / TPR; v < n; v += nthreads / TPR) {
-        const int32_t b = row_ptr[v], e = row_ptr[v + 1];
+    const int64_t total = (int64_t)n + n_items;
+    for (int64_t v = t / TPR; v < total; v += nthreads / TPR) {
+        int32_t row, b, e, slot = -1;
+        if (v < n) {
+            row = (int32_t)v;
+            b = row_ptr[v];
+            e = row_ptr[v + 1];
+            if (e - b >= kSgLong) continue;
+        } else {
+            const int4 it = items[v - n];
+            row = it.x, b = it.y, e = it.z, slot = it.w;
+        }
         float s0 = 0.f, s1 = 0.f;
+#pragma unroll 4
         for (int32_t a = b; a < e; ++a) {
             const bf162 x = reinterpret_cast<const bf162 *>(h + (size_t)__ldg(col + a) * F)[j];
             s0 += __bfloat162float(x.x);
             s1 += __bfloat162float(x.y);
         }
-        const float inv = e > b ? 1.f / (float)(e - b) : 0.f;
-        reinterpret_cast<bf162 *>(m + (size_t)v * F)[j] = __floats2bfloat162_rn(s0 * inv, s1 * inv);
+        if (slot < 0) {
+            const float inv = e > b ? 1.f / (float)(e - b) : 0.f;
+            reinterpret_cast<bf162 *>(m + (size_t)row * F)[j] = __floats2bfloat162_rn(s0 * inv, s1 * inv);
+        } else {
+            atomicAdd(acc + (size_t)slot * F + 2 * j, s0);
+            atomicAdd(acc + (size_t)slot * F + 2 * j + 1, s1);
+        }
+    }
+}
+
+// Long rows: m = acc / d_in, and acc back to zero.
+template <int F>
+__global__ void k_agg_fin(const int32_t *__restrict__ long_rows, int32_t n_long, const int32_t *__restrict__ row_ptr,
+                          float *acc, bf16 *m) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)n_long * (F / 2);
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slot = i / (F / 2);
+        const int j = (int)(i % (F / 2));
+        const int32_t row = long_rows[slot];
+        const float inv = 1.f / (float)(row_ptr[row + 1] - row_ptr[row]);
+        float *p = acc + slot * F + 2 * j;
+        reinterpret_cast<bf162 *>(m + (size_t)row * F)[j] = __floats2bfloat162_rn(p[0] * inv, p[1] * inv);
+        p[0] = p[1] = 0.f;
     }
 }
 
@@ -263,99 +297,206 @@ __global__ void k_head_bwd(const bf16 *__restrict__ h3, const bf16 *__restrict__
     }
 }
 
-// One layer backward for a block of rows: dz = dy * (y > 0); grad Ws += h^T dz,
-// grad Wn += m^T dz, grad b += sum dz; dah = dz Ws^T, dam = dz Wn^T (float32).
-// 256 threads: thread (i, j4) accumulates grad rows i (of 2F) and 4 columns.
+// One layer backward on the tensor cores.  dz = dy * (y > 0) is rounded to bfloat16 and
+// both products take bfloat16 operands with float32 accumulation:
+//   input gradients   [dah | dam] = dz W^T      (rows x 2F, float32 out; skipped for layer 1)
+//   weight gradients  [gWs ; gWn] += [h | m]^T dz   (2F x 64, accumulated in registers)
+//   bias gradient     gb += sum_rows dz          (float32, from the unrounded dz)
+// A CTA of 8 warps walks 32-row tiles staged in shared memory: dz (row-major), the input
+// tile A = [h | m] (row-major) and W = [Ws ; Wn] (2F x 64, row-major, staged once).
+// Fragments for the transposed operands are packed from two bfloat16 half-words.
+__device__ __forceinline__ uint32_t pack_bf16(bf16 lo, bf16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
 template <int F>
 __global__ void __launch_bounds__(256) k_dense_bwd(const bf16 *__restrict__ h, const bf16 *__restrict__ m,
                                                    const bf16 *__restrict__ y, const float *__restrict__ dy,
                                                    const bf16 *__restrict__ Ws, const bf16 *__restrict__ Wn,
-                                                   int32_t n, float *dah, float *dam, float *grad, int l) {
+                                                   int32_t n, float *dah, float *dam, float *grad, int l,
+                                                   int input_grad) {
     constexpr int K = 2 * F;
-    constexpr int ROWS = 16;   // 4 KB dz + 8 KB inputs + 32 KB weights of static shared memory
-    __shared__ float s_dz[ROWS][H];
-    __shared__ float s_a[ROWS][K];
-    __shared__ float s_w[K][H];
+    constexpr int RT = 32;            // rows per tile
+    constexpr int WP = H + 8;         // padded row of W and dz (bank spread)
+    constexpr int AP = K + 8;         // padded row of the input tile
+    constexpr int WT = K / 16 * 8;    // weight-gradient (16 x 8) tiles
+    constexpr int WPW = (WT + 7) / 8; // of them per warp
+    __shared__ __align__(16) bf16 Wsm[K * WP];
+    __shared__ __align__(16) bf16 Zs[RT * WP];
+    __shared__ __align__(16) bf16 As[RT * AP];
+    __shared__ float s_b[8][H];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, tg = lane & 3;
     for (int i = threadIdx.x; i < K * H; i += blockDim.x) {
         const int k = i / H, c = i % H;
-        s_w[k][c] = __bfloat162float(k < F ? Ws[k * H + c] : Wn[(k - F) * H + c]);
+        Wsm[k * WP + c] = k < F ? Ws[k * H + c] : Wn[(k - F) * H + c];
     }
-    // gradient accumulators: K x H entries over 256 threads
-    constexpr int PER = (K * H + 255) / 256;
-    float acc[PER];
+    float wacc[WPW][4];
 #pragma unroll
-    for (int q = 0; q < PER; ++q) acc[q] = 0.f;
-    float accb = 0.f;   // bias column threadIdx.x (< H)
+    for (int j = 0; j < WPW; ++j) wacc[j][0] = wacc[j][1] = wacc[j][2] = wacc[j][3] = 0.f;
+    float gb0 = 0.f, gb1 = 0.f;       // bias columns 2 lane, 2 lane + 1
+    for (int64_t r0 = (int64_t)blockIdx.x * RT; r0 < n; r0 += (int64_t)gridDim.x * RT) {
+        __syncthreads();              // previous tile's readers are done (and W is staged)
+        // dz tile: each thread always handles column pair `lane`
+        for (int rr = warp; rr < RT; rr += 8) {
+            const int64_t r = r0 + rr;
+            float2 d = make_float2(0.f, 0.f);
+            if (r < n) {
+                const float2 v = reinterpret_cast<const float2 *>(dy + (size_t)r * H)[lane];
+                const bf162 yy = reinterpret_cast<const bf162 *>(y + (size_t)r * H)[lane];
+                d.x = __bfloat162float(yy.x) > 0.f ? v.x : 0.f;
+                d.y = __bfloat162float(yy.y) > 0.f ? v.y : 0.f;
+            }
+            gb0 += d.x;
+            gb1 += d.y;
+            *reinterpret_cast<bf162 *>(Zs + rr * WP + 2 * lane) = __floats2bfloat162_rn(d.x, d.y);
+        }
+        for (int i = threadIdx.x; i < RT * (K / 2); i += blockDim.x) {
+            const int rr = i / (K / 2), k = 2 * (i % (K / 2));
+            const int64_t r = r0 + rr;
+            bf162 v = __floats2bfloat162_rn(0.f, 0.f);
+            if (r < n)
+                v = k < F ? reinterpret_cast<const bf162 *>(h + (size_t)r * F + k)[0]
+                          : reinterpret_cast<const bf162 *>(m + (size_t)r * F + (k - F))[0];
+            *reinterpret_cast<bf162 *>(As + rr * AP + k) = v;
+        }
+        __syncthreads();
+        // input gradients: (16-row m-tile, 8-column n-tile) pairs over the warps
+        if (input_grad) {
+            for (int t = warp; t < 2 * (K / 8); t += 8) {
+                const int mt = t & 1, nt = t >> 1;
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int ks = 0; ks < H / 16; ++ks) {
+                    const int c0 = ks * 16 + 2 * tg;
+                    const bf16 *z0 = Zs + (mt * 16 + g) * WP, *z1 = z0 + 8 * WP;
+                    uint32_t a[4];
+                    a[0] = ld_b32(z0 + c0);
+                    a[1] = ld_b32(z1 + c0);
+                    a[2] = ld_b32(z0 + c0 + 8);
+                    a[3] = ld_b32(z1 + c0 + 8);
+                    const bf16 *w = Wsm + (nt * 8 + g) * WP;
+                    mma_bf16(acc, a, ld_b32(w + c0), ld_b32(w + c0 + 8));
+                }
+                const int k = nt * 8 + 2 * tg;
+                const int64_t ra = r0 + mt * 16 + g, rb = ra + 8;
+                float *dst = k < F ? dah : dam;
+                const int kk = k < F ? k : k - F;
+                if (ra < n) *reinterpret_cast<float2 *>(dst + (size_t)ra * F + kk) = make_float2(acc[0], acc[1]);
+                if (rb < n) *reinterpret_cast<float2 *>(dst + (size_t)rb * F + kk) = make_float2(acc[2], acc[3]);
+            }
+        }
+        // weight gradients: A^T (K x RT) times dz (RT x 64), reduction over the tile's rows
+#pragma unroll
+        for (int j = 0; j < WPW; ++j) {
+            const int t = warp + 8 * j;
+            if (t < WT) {
+                const int mt = t >> 3, nt = t & 7;
+                const int ka = mt * 16 + g, cb = nt * 8 + g;
+#pragma unroll
+                for (int ks = 0; ks < RT / 16; ++ks) {
+                    const int rA = ks * 16 + 2 * tg;
+                    uint32_t a[4];
+                    a[0] = pack_bf16(As[rA * AP + ka], As[(rA + 1) * AP + ka]);
+                    a[1] = pack_bf16(As[rA * AP + ka + 8], As[(rA + 1) * AP + ka + 8]);
+                    a[2] = pack_bf16(As[(rA + 8) * AP + ka], As[(rA + 9) * AP + ka]);
+                    a[3] = pack_bf16(As[(rA + 8) * AP + ka + 8], As[(rA + 9) * AP + ka + 8]);
+                    const uint32_t b0 = pack_bf16(Zs[rA * WP + cb], Zs[(rA + 1) * WP + cb]);
+                    const uint32_t b1 = pack_bf16(Zs[(rA + 8) * WP + cb], Zs[(rA + 9) * WP + cb]);
+                    mma_bf16(wacc[j], a, b0, b1);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < WPW; ++j) {
+        const int t = warp + 8 * j;
+        if (t < WT) {
+            const int mt = t >> 3, nt = t & 7;
+            const int c = nt * 8 + 2 * tg;
+            const int ka = mt * 16 + g, kb = ka + 8;
+            float *ga = grad + (ka < F ? off_ws(l) + ka * H : off_wn(l) + (ka - F) * H) + c;
+            float *gbp = grad + (kb < F ? off_ws(l) + kb * H : off_wn(l) + (kb - F) * H) + c;
+            atomicAdd(ga, wacc[j][0]);
+            atomicAdd(ga + 1, wacc[j][1]);
+            atomicAdd(gbp, wacc[j][2]);
+            atomicAdd(gbp + 1, wacc[j][3]);
+        }
+    }
+    s_b[warp][2 * lane] = gb0;
+    s_b[warp][2 * lane + 1] = gb1;
     __syncthreads();
-    for (int64_t r0 = (int64_t)blockIdx.x * ROWS; r0 < n; r0 += (int64_t)gridDim.x * ROWS) {
-        const int rows = (int)min((int64_t)ROWS, (int64_t)n - r0);
-        for (int i = threadIdx.x; i < ROWS * H; i += blockDim.x) {
-            const int rr = i / H, c = i % H;
-            float dz = 0.f;
-            if (rr < rows) {
-                const size_t o = (size_t)(r0 + rr) * H + c;
-                dz = __bfloat162float(y[o]) > 0.f ? dy[o] : 0.f;
-            }
-            s_dz[rr][c] = dz;
-        }
-        for (int i = threadIdx.x; i < ROWS * K; i += blockDim.x) {
-            const int rr = i / K, k = i % K;
-            float a = 0.f;
-            if (rr < rows) a = __bfloat162float(k < F ? h[(size_t)(r0 + rr) * F + k] : m[(size_t)(r0 + rr) * F + (k - F)]);
-            s_a[rr][k] = a;
-        }
-        __syncthreads();
+    if (threadIdx.x < H) {
+        float sb = 0.f;
 #pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int e = threadIdx.x + q * 256;
-            if (e < K * H) {
-                const int k = e / H, c = e % H;
-                float s = 0.f;
-                for (int rr = 0; rr < rows; ++rr) s += s_a[rr][k] * s_dz[rr][c];
-                acc[q] += s;
-            }
-        }
-        if (threadIdx.x < H)
-            for (int rr = 0; rr < rows; ++rr) accb += s_dz[rr][threadIdx.x];
-        // input gradients: thread -> (row, column of 2F)
-        for (int i = threadIdx.x; i < rows * K; i += blockDim.x) {
-            const int rr = i / K, k = i % K;
-            float s = 0.f;
-#pragma unroll 8
-            for (int c = 0; c < H; ++c) s += s_dz[rr][c] * s_w[k][c];
-            if (k < F) dah[(size_t)(r0 + rr) * F + k] = s;
-            else dam[(size_t)(r0 + rr) * F + (k - F)] = s;
-        }
-        __syncthreads();
+        for (int w = 0; w < 8; ++w) sb += s_b[w][threadIdx.x];
+        atomicAdd(grad + off_b(l) + threadIdx.x, sb);
     }
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-        const int e = threadIdx.x + q * 256;
-        if (e < K * H) {
-            const int k = e / H, c = e % H;
-            atomicAdd(grad + (k < F ? off_ws(l) + k * H + c : off_wn(l) + (k - F) * H + c), acc[q]);
-        }
-    }
-    if (threadIdx.x < H) atomicAdd(grad + off_b(l) + threadIdx.x, accb);
 }
 
-// dh_u = dah_u + sum over out-arcs u -> v of dam_v / d_in(v)   (adjoint of the mean)
+// dh_u = dah_u + sum over out-arcs u -> v of dam_v / d_in(v)   (adjoint of the mean).
+// One thread per (item, feature); items as in k_agg but over the out-CSR: long out-rows
+// are skipped here and finished by k_agg_bwd_fin from the chunks' partial sums.
 template <int F>
-__global__ void k_agg_bwd(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ out_ptr,
-                          const int32_t *__restrict__ out_dst, int32_t n, const float *__restrict__ dah,
-                          const float *__restrict__ dam, float *dh) {
+__global__ void k_agg_bwd(const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ out_dst,
+                          const float *__restrict__ inv_din, int32_t n, const float *__restrict__ dah,
+                          const float *__restrict__ dam, float *dh, const int4 *__restrict__ items,
+                          int32_t n_items, float *acc) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = t; i < (int64_t)n * F; i += nthreads) {
-        const int64_t u = i / F;
+    const int64_t total = ((int64_t)n + n_items) * F;
+    for (int64_t i = t; i < total; i += nthreads) {
+        const int64_t v = i / F;
         const int j = (int)(i % F);
-        float s = dah[i];
-        const int32_t b = out_ptr[u], e = out_ptr[u + 1];
-        for (int32_t a = b; a < e; ++a) {
-            const int32_t v = out_dst[a];
-            s += dam[(size_t)v * F + j] / (float)(row_ptr[v + 1] - row_ptr[v]);
+        int32_t u, b, e, slot = -1;
+        if (v < n) {
+            u = (int32_t)v;
+            b = out_ptr[v];
+            e = out_ptr[v + 1];
+            if (e - b >= kSgLong) continue;
+        } else {
+            const int4 it = items[v - n];
+            u = it.x, b = it.y, e = it.z, slot = it.w;
         }
-        dh[i] = s;
+        float s = 0.f;
+#pragma unroll 4
+        for (int32_t a = b; a < e; ++a) {
+            const int32_t w = __ldg(out_dst + a);
+            s += dam[(size_t)w * F + j] * __ldg(inv_din + w);
+        }
+        if (slot < 0) dh[(size_t)u * F + j] = dah[(size_t)u * F + j] + s;
+        else atomicAdd(acc + (size_t)slot * F + j, s);
+    }
+}
+
+template <int F>
+__global__ void k_agg_bwd_fin(const int32_t *__restrict__ long_rows, int32_t n_long, const float *__restrict__ dah,
+                              float *acc, float *dh) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)n_long * F;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slot = i / F;
+        const int j = (int)(i % F);
+        const size_t o = (size_t)long_rows[slot] * F + j;
+        dh[o] = dah[o] + acc[i];
+        acc[i] = 0.f;
+    }
+}
+
+// Per-graph tables: 1 / d_in and the long rows of a CSR.
+__global__ void k_inv_deg(const int32_t *__restrict__ row_ptr, int32_t n, float *inv) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = row_ptr[v + 1] - row_ptr[v];
+        inv[v] = d > 0 ? 1.f / (float)d : 0.f;
+    }
+}
+
+__global__ void k_long_rows(const int32_t *__restrict__ ptr, int32_t n, int32_t cap, int4 *out, int32_t *count) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t b = ptr[v], e = ptr[v + 1];
+        if (e - b >= kSgLong) {
+            const int32_t i = atomicAdd(count, 1);
+            if (i < cap) out[i] = make_int4((int32_t)v, b, e, 0);
+        }
     }
 }
 
@@ -444,18 +585,96 @@ int grid_of(const fsgp_surrogate *s, int64_t work, int threads, int per_sm = 8) 
     return (int)std::max<int64_t>(g, 1);
 }
 
+// Long rows of one CSR (ptr) as chunk items and a slot -> row list (host build, once).
+int sg_long_table(const int32_t *ptr, int32_t n, int64_t nnz, int sm_count, int4 **items, int32_t *n_items,
+                  int32_t **long_rows, int32_t *n_long) {
+    const int64_t cap = nnz / kSgLong + 1;
+    int4 *d_tmp = nullptr;
+    int32_t *d_cnt = nullptr;
+    FSGP_CUDA(cudaMalloc(&d_tmp, sizeof(int4) * (size_t)cap));
+    cudaError_t e = cudaMalloc(&d_cnt, sizeof(int32_t));
+    int32_t cnt = 0;
+    std::vector<int4> rows;
+    if (e == cudaSuccess) e = cudaMemset(d_cnt, 0, sizeof(int32_t));
+    if (e == cudaSuccess) {
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)sm_count * 8));
+        k_long_rows<<<grid, 256>>>(ptr, n, (int32_t)cap, d_tmp, d_cnt);
+        e = cudaMemcpy(&cnt, d_cnt, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    }
+    if (e == cudaSuccess && cnt > 0) {
+        rows.resize((size_t)cnt);
+        e = cudaMemcpy(rows.data(), d_tmp, sizeof(int4) * (size_t)cnt, cudaMemcpyDeviceToHost);
+    }
+    cudaFree(d_tmp);
+    cudaFree(d_cnt);
+    if (e != cudaSuccess) return cuda_fail(e, "surrogate long rows");
+    std::sort(rows.begin(), rows.end(), [](const int4 &x, const int4 &y) { return x.x < y.x; });
+    std::vector<int4> it;
+    std::vector<int32_t> lr;
+    for (size_t sl = 0; sl < rows.size(); ++sl) {
+        lr.push_back(rows[sl].x);
+        for (int32_t b = rows[sl].y; b < rows[sl].z; b += kSgChunk)
+            it.push_back(make_int4(rows[sl].x, b, std::min(b + kSgChunk, rows[sl].z), (int32_t)sl));
+    }
+    *n_items = (int32_t)it.size();
+    *n_long = (int32_t)lr.size();
+    if (!it.empty()) {
+        FSGP_CUDA(cudaMalloc(items, sizeof(int4) * it.size()));
+        FSGP_CUDA(cudaMemcpy(*items, it.data(), sizeof(int4) * it.size(), cudaMemcpyHostToDevice));
+        FSGP_CUDA(cudaMalloc(long_rows, sizeof(int32_t) * lr.size()));
+        FSGP_CUDA(cudaMemcpy(*long_rows, lr.data(), sizeof(int32_t) * lr.size(), cudaMemcpyHostToDevice));
+    }
+    return FSGP_OK;
+}
+
+// Build the graph's aggregation tables on first use (synchronous; call outside captures).
+int sg_cache(const fsgp_graph *gc, int sm_count) {
+    fsgp_graph *g = const_cast<fsgp_graph *>(gc);   // lazily built cache of the handle
+    SgCache &C = g->sgc;
+    if (C.built) return FSGP_OK;
+    FSGP_CUDA(cudaMalloc(&C.inv_din, sizeof(float) * (size_t)g->n));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->n + 255) / 256, (int64_t)sm_count * 8));
+    k_inv_deg<<<grid, 256>>>(g->row_ptr, g->n, C.inv_din);
+    int rc = sg_long_table(g->row_ptr, g->n, g->nnz, sm_count, &C.in_items, &C.n_in_items, &C.in_long, &C.n_in_long);
+    if (rc) return rc;
+    rc = sg_long_table(g->out_ptr, g->n, g->nnz, sm_count, &C.out_items, &C.n_out_items, &C.out_long, &C.n_out_long);
+    if (rc) return rc;
+    const size_t nl = (size_t)std::max(C.n_in_long, C.n_out_long);
+    if (nl) {
+        FSGP_CUDA(cudaMalloc(&C.acc, sizeof(float) * nl * H));
+        FSGP_CUDA(cudaMemset(C.acc, 0, sizeof(float) * nl * H));
+    }
+    FSGP_CUDA(cudaDeviceSynchronize());
+    C.built = 1;
+    return FSGP_OK;
+}
+
 // Forward of the three layers and the head from features s->x (already seeded).
 void sg_forward(fsgp_surrogate *s, const fsgp_graph *g, float *p, float *psum, cudaStream_t st) {
     const int32_t n = g->n;
     const bf16 *W = s->wb;
     const float *B = s->theta;
-    k_agg<F0><<<grid_of(s, (int64_t)n * (F0 / 2), 256), 256, 0, st>>>(g->row_ptr, g->col, n, s->x, s->m1);
+    const SgCache &C = g->sgc;
+    const int64_t items = (int64_t)n + C.n_in_items;
+    k_agg<F0><<<grid_of(s, items * (F0 / 2), 256), 256, 0, st>>>(g->row_ptr, g->col, n, s->x, s->m1, C.in_items,
+                                                                 C.n_in_items, C.acc);
+    if (C.n_in_long)
+        k_agg_fin<F0><<<grid_of(s, (int64_t)C.n_in_long * (F0 / 2), 256), 256, 0, st>>>(C.in_long, C.n_in_long,
+                                                                                     g->row_ptr, C.acc, s->m1);
     k_dense<F0><<<grid_of(s, ((int64_t)n + 63) / 64 * 128, 128, 16), 128, 0, st>>>(
         s->x, s->m1, W + OFF_WS1, W + OFF_WN1, B + OFF_B1, n, s->h1);
-    k_agg<H><<<grid_of(s, (int64_t)n * (H / 2), 256), 256, 0, st>>>(g->row_ptr, g->col, n, s->h1, s->m2);
+    k_agg<H><<<grid_of(s, items * (H / 2), 256), 256, 0, st>>>(g->row_ptr, g->col, n, s->h1, s->m2, C.in_items,
+                                                              C.n_in_items, C.acc);
+    if (C.n_in_long)
+        k_agg_fin<H><<<grid_of(s, (int64_t)C.n_in_long * (H / 2), 256), 256, 0, st>>>(C.in_long, C.n_in_long,
+                                                                                   g->row_ptr, C.acc, s->m2);
     k_dense<H><<<grid_of(s, ((int64_t)n + 63) / 64 * 128, 128, 16), 128, 0, st>>>(
         s->h1, s->m2, W + OFF_WS2, W + OFF_WN2, B + OFF_B2, n, s->h2);
-    k_agg<H><<<grid_of(s, (int64_t)n * (H / 2), 256), 256, 0, st>>>(g->row_ptr, g->col, n, s->h2, s->m3);
+    k_agg<H><<<grid_of(s, items * (H / 2), 256), 256, 0, st>>>(g->row_ptr, g->col, n, s->h2, s->m3, C.in_items,
+                                                              C.n_in_items, C.acc);
+    if (C.n_in_long)
+        k_agg_fin<H><<<grid_of(s, (int64_t)C.n_in_long * (H / 2), 256), 256, 0, st>>>(C.in_long, C.n_in_long,
+                                                                                   g->row_ptr, C.acc, s->m3);
     k_dense<H><<<grid_of(s, ((int64_t)n + 63) / 64 * 128, 128, 16), 128, 0, st>>>(
         s->h2, s->m3, W + OFF_WS3, W + OFF_WN3, B + OFF_B3, n, s->h3);
     k_head<<<grid_of(s, (int64_t)n * 32, 256), 256, 0, st>>>(s->h3, W + OFF_WO, B + OFF_BO, n, p, psum, s->cur);
@@ -467,6 +686,8 @@ int sg_prepare_inputs(fsgp_surrogate *s, const fsgp_graph *g, const int32_t *see
         if (seeds_host[i] < 0 || seeds_host[i] >= g->n) return fail(FSGP_EINVAL, "seed node out of range");
     int rc = sg_ensure(s, g->n);
     if (rc) return rc;
+    rc = sg_cache(g, s->sm_count);
+    if (rc) return rc;
     k_features<<<grid_of(s, g->n, 256), 256, 0, st>>>(g->row_ptr, g->out_ptr, g->n, (float)beta, (float)gamma, s->x);
     if (ns > 0) {
         // seed bits: small host list staged through the activation buffer y (floats)
@@ -475,7 +696,7 @@ int sg_prepare_inputs(fsgp_surrogate *s, const fsgp_graph *g, const int32_t *see
         FSGP_CUDA(cudaMemcpyAsync(d_seeds, seeds_host, sizeof(int32_t) * (size_t)ns, cudaMemcpyHostToDevice, st));
         FSGP_CUDA(cudaMemsetAsync(s->cur, 0, sizeof(int32_t), st));
         k_seed_bits<<<1, 256, 0, st>>>(d_seeds, (int32_t)ns, s->cur, 1.f, 0, s->x);
-        const int gk = (int)std::min<int64_t>(((int64_t)ns * 32 + 255) / 256, 1024);
+        const int gk = (int)std::min<int64_t>(ns, 1024);
         k_seed_count<<<gk, 256, 0, st>>>(d_seeds, (int32_t)ns, s->cur, g->out_ptr, g->out_dst, 1, s->cnt);
         k_seed_feat<<<gk, 256, 0, st>>>(d_seeds, (int32_t)ns, s->cur, g->out_ptr, g->out_dst, s->cnt, s->x);
         k_seed_count<<<gk, 256, 0, st>>>(d_seeds, (int32_t)ns, s->cur, g->out_ptr, g->out_dst, -1, s->cnt);
@@ -490,15 +711,25 @@ int sg_backward(fsgp_surrogate *s, const fsgp_graph *g, cudaStream_t st) {
     FSGP_CUDA(cudaMemsetAsync(s->grad, 0, sizeof(float) * N_PARAMS, st));
     FSGP_CUDA(cudaMemsetAsync(s->loss, 0, sizeof(double), st));
     k_head_bwd<<<grid_of(s, (int64_t)n * 32, 256), 256, 0, st>>>(s->h3, W + OFF_WO, s->p, s->y, n, s->dh, s->grad, s->loss);
-    const int gb = grid_of(s, (int64_t)n, 16, 2);
+    const int gb = grid_of(s, ((int64_t)n + 31) / 32, 1, 2);
     // layer 3: dy = dh (float), outputs dh2 = d h2
-    k_dense_bwd<H><<<gb, 256, 0, st>>>(s->h2, s->m3, s->h3, s->dh, W + OFF_WS3, W + OFF_WN3, n, s->dah, s->dam, s->grad, 3);
-    k_agg_bwd<H><<<grid_of(s, (int64_t)n * H, 256), 256, 0, st>>>(g->row_ptr, g->out_ptr, g->out_dst, n, s->dah, s->dam, s->dh2);
+    k_dense_bwd<H><<<gb, 256, 0, st>>>(s->h2, s->m3, s->h3, s->dh, W + OFF_WS3, W + OFF_WN3, n, s->dah, s->dam, s->grad, 3, 1);
+    const SgCache &C = g->sgc;
+    const int64_t items = (int64_t)n + C.n_out_items;
+    k_agg_bwd<H><<<grid_of(s, items * H, 256), 256, 0, st>>>(g->out_ptr, g->out_dst, C.inv_din, n, s->dah, s->dam,
+                                                            s->dh2, C.out_items, C.n_out_items, C.acc);
+    if (C.n_out_long)
+        k_agg_bwd_fin<H><<<grid_of(s, (int64_t)C.n_out_long * H, 256), 256, 0, st>>>(C.out_long, C.n_out_long,
+                                                                                  s->dah, C.acc, s->dh2);
     // layer 2
-    k_dense_bwd<H><<<gb, 256, 0, st>>>(s->h1, s->m2, s->h2, s->dh2, W + OFF_WS2, W + OFF_WN2, n, s->dah, s->dam, s->grad, 2);
-    k_agg_bwd<H><<<grid_of(s, (int64_t)n * H, 256), 256, 0, st>>>(g->row_ptr, g->out_ptr, g->out_dst, n, s->dah, s->dam, s->dh);
+    k_dense_bwd<H><<<gb, 256, 0, st>>>(s->h1, s->m2, s->h2, s->dh2, W + OFF_WS2, W + OFF_WN2, n, s->dah, s->dam, s->grad, 2, 1);
+    k_agg_bwd<H><<<grid_of(s, items * H, 256), 256, 0, st>>>(g->out_ptr, g->out_dst, C.inv_din, n, s->dah, s->dam,
+                                                            s->dh, C.out_items, C.n_out_items, C.acc);
+    if (C.n_out_long)
+        k_agg_bwd_fin<H><<<grid_of(s, (int64_t)C.n_out_long * H, 256), 256, 0, st>>>(C.out_long, C.n_out_long,
+                                                                                  s->dah, C.acc, s->dh);
     // layer 1 (input gradients not needed beyond the weights)
-    k_dense_bwd<F0><<<gb, 256, 0, st>>>(s->x, s->m1, s->h1, s->dh, W + OFF_WS1, W + OFF_WN1, n, s->dah, s->dam, s->grad, 1);
+    k_dense_bwd<F0><<<gb, 256, 0, st>>>(s->x, s->m1, s->h1, s->dh, W + OFF_WS1, W + OFF_WN1, n, s->dah, s->dam, s->grad, 1, 0);
     FSGP_CUDA(cudaGetLastError());
     return FSGP_OK;
 }
@@ -663,6 +894,8 @@ extern "C" int fsgp_surrogate_screen(fsgp_surrogate *s, const fsgp_graph *g, con
     cudaStream_t caller = (cudaStream_t)stream;
     int rc = sg_ensure(s, g->n);
     if (rc) return rc;
+    rc = sg_cache(g, s->sm_count);
+    if (rc) return rc;
     // captures are not allowed on the legacy default stream: work on a private stream
     // ordered after the caller's work
     cudaStream_t st = nullptr;
@@ -696,7 +929,7 @@ extern "C" int fsgp_surrogate_screen(fsgp_surrogate *s, const fsgp_graph *g, con
             rc = cuda_fail(e, "capture");
             break;
         }
-        const int gk = (int)std::min<int64_t>(((int64_t)k * 32 + 255) / 256, 1024);
+        const int gk = std::min<int32_t>(k, 1024);
         k_seed_bits<<<1, 256, 0, st>>>(d_cand, k, s->cur, 1.f, 0, s->x);
         k_seed_count<<<gk, 256, 0, st>>>(d_cand, k, s->cur, g->out_ptr, g->out_dst, 1, s->cnt);
         k_seed_feat<<<gk, 256, 0, st>>>(d_cand, k, s->cur, g->out_ptr, g->out_dst, s->cnt, s->x);

@@ -95,6 +95,8 @@ def load():
         lib.fsgp_graph_destroy.restype = ctypes.c_int
         lib.fsgp_graph_info.argtypes = [P, P, P, P, P]
         lib.fsgp_graph_info.restype = ctypes.c_int
+        lib.fsgp_graph_trim.argtypes = [P]
+        lib.fsgp_graph_trim.restype = ctypes.c_int
         lib.fsgp_model_planes.argtypes = [ctypes.c_int32]
         lib.fsgp_model_planes.restype = ctypes.c_int
         lib.fsgp_simulate.argtypes = [P, ctypes.c_int32, ctypes.POINTER(fsgp_params), P, P,
@@ -192,6 +194,10 @@ def fsgp_graph_destroy(h) -> None:
     _check(load().fsgp_graph_destroy(h))
 
 
+def fsgp_graph_trim(h) -> None:
+    _check(load().fsgp_graph_trim(h))
+
+
 def fsgp_graph_info(h) -> dict:
     n = ctypes.c_int32()
     nnz = ctypes.c_int64()
@@ -257,6 +263,10 @@ class Graph:
 
     def info(self) -> dict:
         return fsgp_graph_info(self.handle)
+
+    def trim(self) -> None:
+        """Free the cached simulation workspace (fsgp_graph_trim)."""
+        fsgp_graph_trim(self.handle)
 
     def close(self):
         if getattr(self, "handle", None) is not None:
@@ -419,15 +429,18 @@ class Surrogate:
                                           _stream_handle(stream)))
         return loss.value, g
 
-    def train_step(self, graph, seeds, beta, gamma, y, lr=1e-3, stream=None):
+    def train_step(self, graph, seeds, beta, gamma, y, lr=1e-3, stream=None, want_loss=True):
+        """One Adam step; returns the loss before the step (synchronising the stream), or
+        None without a synchronisation when want_loss is False."""
         seeds = np.ascontiguousarray(seeds, dtype=np.int32)
         loss = ctypes.c_double(0.0)
         _check(load().fsgp_surrogate_train_step(self.handle, graph.handle,
                                                 seeds.ctypes.data if seeds.size else None,
                                                 seeds.size, beta, gamma, _ptr(y),
-                                                ctypes.c_float(lr), ctypes.byref(loss),
+                                                ctypes.c_float(lr),
+                                                ctypes.byref(loss) if want_loss else None,
                                                 _stream_handle(stream)))
-        return loss.value
+        return loss.value if want_loss else None
 
     def screen(self, graph, candidates, beta, gamma, stream=None) -> np.ndarray:
         c = np.ascontiguousarray(candidates, dtype=np.int32)

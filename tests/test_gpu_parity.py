@@ -234,6 +234,24 @@ def test_host_result_buffers(cuda_lib):
         assert np.array_equal(np.asarray(h[k]).view(d[k].dtype), d[k]), k
 
 
+def test_trim_frees_workspace_and_keeps_results(cuda_lib):
+    """fsgp_graph_trim drops the cached workspace; the next run re-allocates it and gives
+    the same bits."""
+    wl = W.er10k_sir()
+    graph = cuda_lib.Graph(wl.graph.row_ptr, wl.graph.col_idx)
+    a = gpu_run(cuda_lib, wl.graph, O.SIR, wl.seed_sets, wl.R, wl.T, wl.rng_seed, graph_obj=graph,
+                beta=wl.beta, gamma=wl.gamma)
+    grown = graph.info()["device_bytes"]
+    graph.trim()
+    assert graph.info()["device_bytes"] < grown
+    graph.trim()                       # idempotent
+    b = gpu_run(cuda_lib, wl.graph, O.SIR, wl.seed_sets, wl.R, wl.T, wl.rng_seed, graph_obj=graph,
+                beta=wl.beta, gamma=wl.gamma)
+    assert graph.info()["device_bytes"] == grown
+    for k in ("counts", "freq", "per_real", "final_planes"):
+        assert np.array_equal(a[k], b[k]), k
+
+
 # ---------------------------------------------------------- larger workloads
 
 @pytest.mark.parametrize("model", [O.IC, O.LT])

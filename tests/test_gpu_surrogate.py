@@ -56,6 +56,49 @@ def test_gradient_matches_reference(cuda_lib):
         o += k
 
 
+def _hub_graphs():
+    """Graphs with rows far above the 256-arc split: R-MAT scale 12 (hubs of thousands of
+    in- and out-arcs) and a BA graph plus a star whose row lengths (1000 in, 700 out) end
+    in ragged chunks."""
+    r = W.rmat(12, 16, seed=77)
+    b = W.ba(2000, 3, seed=78)
+    n = b.n
+    dst = np.repeat(np.arange(n), np.diff(b.row_ptr))
+    src = b.col_idx
+    src = np.concatenate([src, np.arange(1, 1001), np.zeros(700, dtype=np.int64)])
+    dst = np.concatenate([dst, np.zeros(1000, dtype=np.int64), np.arange(1, 701)])
+    return [r, W.from_arcs(n, src, dst, "ba_star")]
+
+
+@pytest.mark.parametrize("gi", [0, 1])
+def test_long_rows_forward_and_gradient(cuda_lib, gi):
+    import torch
+    f = cuda_lib
+    g = _hub_graphs()[gi]
+    din = np.diff(g.row_ptr)
+    dout = np.bincount(g.col_idx, minlength=g.n)
+    assert din.max() >= 700 and dout.max() >= 700
+    graph = f.Graph(g.row_ptr, g.col_idx)
+    sg = f.Surrogate(21)
+    theta = S.init_params(22).astype(np.float32)
+    sg.set_params(theta)
+    seeds = np.array([0, int(np.argmax(dout)), 5, 9], dtype=np.int32)
+    p = sg.forward(graph, seeds, 0.05, 0.1).cpu().numpy()
+    x = S.features(g.row_ptr, g.col_idx, seeds, 0.05, 0.1)
+    ref, _ = S.forward(theta.astype(np.float64), g.row_ptr, g.col_idx, x, bf16=True)
+    err = np.abs(p - ref)
+    assert err.max() <= 1e-2 and err.mean() <= 1e-3, (err.max(), err.mean())
+    y = np.random.default_rng(3).random(g.n).astype(np.float32)
+    loss, grad = sg.grad(graph, seeds, 0.05, 0.1, torch.from_numpy(y).cuda())
+    rl, rg = S.loss_and_grad(theta.astype(np.float64), g.row_ptr, g.col_idx, x, y.astype(np.float64),
+                             bf16=True)
+    assert abs(loss - rl) <= 1e-3 * abs(rl)
+    assert np.linalg.norm(grad - rg) <= 2e-2 * np.linalg.norm(rg)
+    # a second call reuses the graph's cleared accumulators: same result
+    p2 = sg.forward(graph, seeds, 0.05, 0.1).cpu().numpy()
+    assert np.abs(p2 - p).max() <= 5e-3   # float32 atomics may reorder a sum
+
+
 def test_adam_step_matches_reference(cuda_lib):
     import torch
     f = cuda_lib

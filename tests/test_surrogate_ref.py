@@ -67,6 +67,10 @@ def test_seed_in_arc_feature_brute_force():
     assert np.array_equal(x[:, 0], [1, 0, 1, 0, 0])
     assert np.allclose(x[:, 3], np.log1p([1, 3, 1, 1, 1]))   # in-degrees
     assert np.allclose(x[:, 4], np.log1p([3, 1, 1, 1, 1]))   # out-degrees
+    # a seed listed twice counts twice
+    x2 = S.features(g.row_ptr, g.col_idx, np.array([0, 2, 0], dtype=np.int32), 0.1, 0.2)
+    assert np.allclose(x2[:, 5], np.log1p([0, 5, 0, 2, 0]))
+    assert np.array_equal(x2[:, 0], x[:, 0])
 
 
 def test_bf16_rounding():

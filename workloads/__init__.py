@@ -254,3 +254,50 @@ def batch_pool(n_graphs: int = 64, n_requests: int = 4096, n_min: int = 1_000,
             R=Rs[int(hash64(seed, 8, j) % len(Rs))], T=T,
             beta=0.005 + 0.195 * uniform01(seed, 9, j), gamma=0.1, rng_seed=1 + j))
     return graphs, reqs
+
+
+# ------------------------------------------------------------ surrogate training pool
+
+def surrogate_pool(n_graphs: int = 200, n_min: int = 100_000, n_max: int = 1_000_000,
+                   seed: int = 12345 + 5, threads: int | None = None):
+    """Synthetic graphs for training and judging the seed-set surrogate: even indices
+    are BA graphs (both arc directions, m in 2..6, n log-uniform in [n_min, n_max]),
+    odd indices directed R-MAT graphs (a, b, c = 0.57, 0.19, 0.19, edge factor 8,
+    scale in 17..19, i.e. n = 131,072 .. 524,288).  Generated in parallel threads."""
+    from concurrent.futures import ThreadPoolExecutor
+    lo, hi = np.log(n_min), np.log(n_max)
+
+    def make(i):
+        if i % 2 == 0:
+            n = int(round(np.exp(lo + (hi - lo) * uniform01(seed, 1, i))))
+            m = 2 + int(hash64(seed, 2, i) % 5)
+            return ba(n, m, seed=seed * 1000 + i)
+        scale = 17 + int(hash64(seed, 3, i) % 3)
+        return rmat(scale, 8, 0.57, 0.19, 0.19, seed=seed * 1000 + i, nthreads=1)
+
+    with ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 1) as ex:
+        return list(ex.map(make, range(n_graphs)))
+
+
+def surrogate_sets(g: Graph, gi: int, n_sets: int = 8, k: int = 20, seed: int = 12345 + 6):
+    """Training seed sets for graph gi: n_sets uniform random k-node sets, each with
+    beta ~ U[0.01, 0.1] (gamma = 0.1 is fixed by the caller)."""
+    out = []
+    for j in range(n_sets):
+        s = seed_set(g.n, k, seed=seed * 1_000_000 + gi * 1000 + j)
+        out.append((s, 0.01 + 0.09 * uniform01(seed, gi, j)))
+    return out
+
+
+def surrogate_candidates(g: Graph, n_cand: int = 10_000, k: int = 20, seed: int = 0):
+    """Candidate k-node seed sets for screening: candidate c takes round(k f_c) of its
+    nodes by sampling arcs uniformly (a node with probability proportional to its
+    out-degree) and the rest uniformly, f_c ~ U[0, 1], so candidates range from random
+    sets to hub-heavy ones.  Nodes may repeat within a candidate."""
+    rng = np.random.default_rng(seed)
+    f = rng.random(n_cand)
+    nb = np.rint(k * f).astype(np.int64)
+    biased = g.col_idx[rng.integers(0, g.nnz, size=(n_cand, k))]
+    uniform = rng.integers(0, g.n, size=(n_cand, k), dtype=np.int64)
+    take = np.arange(k)[None, :] < nb[:, None]
+    return np.where(take, biased, uniform).astype(np.int32)
