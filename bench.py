@@ -518,7 +518,8 @@ def main():
     graph = fsgp.Graph(g.row_ptr, g.col_idx)
     torch.cuda.synchronize()
     log(f"[bench] graph on device in {time.time() - t0:.1f}s: {graph.info()}")
-    r_offset = rank * R
+    from paper_2603_14895_gb300.shard import lane_shard
+    r_offset, _ = lane_shard(R * world, world, rank)     # weak scaling: R lanes per rank
     stream = torch.cuda.current_stream()
     outs = {m: fsgp.simulate(graph, m, [seeds], R, T, RNG_SEED, beta=BETA, gamma=GAMMA,
                              freq=True, device=True,
