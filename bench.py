@@ -475,6 +475,7 @@ def main():
     ap.add_argument("--sg-cands", type=int, default=10_000)
     ap.add_argument("--sg-screen-graphs", type=int, default=4)
     ap.add_argument("--sg-beta-screen", type=float, default=0.01)
+    ap.add_argument("--single-reps", type=int, default=2)
     ap.add_argument("--batch-graphs", type=int, default=64)
     ap.add_argument("--batch-requests", type=int, default=4096)
     args = ap.parse_args()
@@ -578,6 +579,33 @@ def main():
     for m, nm in zip(MODELS, ("SIR", "SIS")):
         wall[nm] = sum(profiles[m].ms) / args.steps / 1e3
 
+    # the plain single-instance path (one realization, one byte per node) on the same
+    # graph: a few realizations timed, the full R-realization run extrapolated
+    single = None
+    if args.single_reps > 0:
+        ms_single = {}
+        for m, nm in zip(MODELS, ("SIR", "SIS")):
+            fsgp.simulate_single(graph, m, seeds, r_offset, T, RNG_SEED, beta=BETA, gamma=GAMMA,
+                                 final_state=False)          # warm-up (workspace)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(args.single_reps):
+                fsgp.simulate_single(graph, m, seeds, r_offset + i, T, RNG_SEED, beta=BETA,
+                                     gamma=GAMMA, final_state=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_single[nm] = e0.elapsed_time(e1) / args.single_reps
+        extrap_s = sum(ms_single.values()) * R / 1e3
+        single = {"realizations_timed_per_model": args.single_reps,
+                  "ms_per_realization": ms_single,
+                  "full_mc_s_extrapolated": extrap_s,
+                  "packed_full_mc_s": ms_per_step / 1e3,
+                  "packed_speedup": extrap_s / (ms_per_step / 1e3),
+                  "note": "single-instance time x R (extrapolated); same draws as packed lanes"}
+        log(f"[bench] single-instance: {ms_single} ms/realization; full MC extrapolated "
+            f"{extrap_s:.1f}s vs packed {ms_per_step / 1e3:.2f}s")
+
     # end to end through the public API with host buffers (graph upload included)
     e2e = None
     if not args.no_e2e:
@@ -630,6 +658,7 @@ def main():
         "sparse_steps": sum(profiles[m].sparse_steps for m in MODELS) // args.steps,
         "clocks": clocks,
         "e2e": e2e,
+        "single_instance": single,
         "gpu_launches": int(launches),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -185,6 +185,24 @@ int fsgp_simulate(const fsgp_graph *g, int32_t model, const fsgp_params *params,
                   uint32_t seed_flags, int32_t R, int32_t T, uint64_t rng_seed,
                   const fsgp_options *opt, fsgp_result *out, void *stream);
 
+/* The plain single-instance path: ONE realization (global index r, any r >= 0) with one
+ * byte of state per node and no bit packing, the per-node update of Sec. 2 (Eq.
+ * nodestate) run as it is written.  Its draws are those of lane r of fsgp_simulate, so
+ * its states and counts equal that lane's exactly; it exists as the baseline the packed
+ * path is measured against.
+ *   seed_nodes: n_seeds nodes, host or device per seed_flags.
+ *   counts:      [T+1][3] u64 compartment counts (required).
+ *   final_state: [n] u8 state after the run, 0/1/2 as in the compartment table (optional).
+ *   steps_run:   transitions computed (IC/LT stop at the first step that activates
+ *                nothing; later rows repeat), optional.
+ *   All outputs host or all device per out_flags.  Synchronises the stream.
+ * Errors: EINVAL (bad arguments, seed out of range), ENOMEM, ECUDA. */
+int fsgp_simulate_single(const fsgp_graph *g, int32_t model, const fsgp_params *params,
+                         const int32_t *seed_nodes, int64_t n_seeds, uint32_t seed_flags,
+                         int32_t r, int32_t T, uint64_t rng_seed, uint64_t *counts,
+                         uint8_t *final_state, int32_t *steps_run, uint32_t out_flags,
+                         void *stream);
+
 /* One request of a batch (fsgp_batch_run). */
 typedef struct {
     const fsgp_graph *graph;

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "fsgp.h"
 
@@ -136,6 +137,14 @@ struct fsgp_graph {
 
 namespace fsgp {
 // thread-local error message
+// Host helpers shared by the simulation entry points (simulate.cu).
+// Grow the graph's cached workspace to at least `bytes` (contents undefined).
+int ensure_workspace(fsgp_graph *g, size_t bytes);
+// Exact integer survival table surv[k] ~ 2^32 (1 - beta)^k for k = 0 .. min(K_sat,
+// max_deg), where surv[K_sat] = 0 (every lane with k >= K_sat is infected); ksat =
+// INT32_MAX when the table never reaches 0 within max_deg.
+void survival_table(double beta, int32_t max_deg, std::vector<uint64_t> &out, int32_t *ksat);
+
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);

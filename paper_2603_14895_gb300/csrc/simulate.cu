@@ -353,7 +353,7 @@ static int ensure_hub_table(fsgp_graph *g, int hub_min_deg, int chunk, cudaStrea
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static int ensure_workspace(fsgp_graph *g, size_t bytes) {
+int ensure_workspace(fsgp_graph *g, size_t bytes) {
     if (g->ws.bytes >= bytes) return FSGP_OK;
     cudaFree(g->ws.ptr);
     g->ws.ptr = nullptr;
@@ -391,7 +391,7 @@ static int words_per_set(int R) {
 
 // Survival table for one beta, up to min(K_sat, max in-degree); ksat = INT32_MAX if the
 // table never reaches zero.
-static void survival_table(double beta, int32_t max_deg, std::vector<uint64_t> &out, int32_t *ksat) {
+void survival_table(double beta, int32_t max_deg, std::vector<uint64_t> &out, int32_t *ksat) {
     const uint64_t b = (uint64_t)llrint(beta * 4294967296.0);
     const uint64_t q = TWO32 - b;
     out.push_back(TWO32);

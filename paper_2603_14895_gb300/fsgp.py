@@ -95,6 +95,10 @@ def load():
         lib.fsgp_graph_destroy.restype = ctypes.c_int
         lib.fsgp_graph_info.argtypes = [P, P, P, P, P]
         lib.fsgp_graph_info.restype = ctypes.c_int
+        lib.fsgp_simulate_single.argtypes = [P, ctypes.c_int32, ctypes.POINTER(fsgp_params), P,
+                                             ctypes.c_int64, ctypes.c_uint32, ctypes.c_int32,
+                                             ctypes.c_int32, ctypes.c_uint64, P, P, P, ctypes.c_uint32, P]
+        lib.fsgp_simulate_single.restype = ctypes.c_int
         lib.fsgp_graph_trim.argtypes = [P]
         lib.fsgp_graph_trim.restype = ctypes.c_int
         lib.fsgp_model_planes.argtypes = [ctypes.c_int32]
@@ -347,6 +351,27 @@ def simulate(graph: Graph, model: int, seed_sets, R: int, T: int, rng_seed: int,
         options = make_options(**options)
     fsgp_simulate(graph.handle, model, prm, seeds, offs, n_sets, PTR_HOST, R, T, rng_seed,
                   options, res, stream)
+    return out
+
+
+def simulate_single(graph: Graph, model: int, seeds, r: int, T: int, rng_seed: int, *, beta=0.0,
+                    gamma=0.0, ic_mode=IC_WEIGHTED_CASCADE, ic_p=0.0, final_state=True, stream=None):
+    """The plain single-instance path (fsgp_simulate_single) for realization r; returns
+    device tensors counts [T+1][3] (int64), final_state [n] (uint8) and steps_run."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    counts = torch.zeros((T + 1, 3), dtype=torch.int64, device=dev)
+    fs = torch.zeros(graph.n, dtype=torch.uint8, device=dev) if final_state else None
+    sr = torch.zeros(1, dtype=torch.int32, device=dev)
+    prm = fsgp_params(beta=beta, gamma=gamma, ic_mode=ic_mode, ic_p=ic_p)
+    _check(load().fsgp_simulate_single(graph.handle, model, ctypes.byref(prm),
+                                       seeds.ctypes.data if seeds.size else None, seeds.size, PTR_HOST,
+                                       r, T, rng_seed, _ptr(counts), _ptr(fs), _ptr(sr), PTR_DEVICE,
+                                       _stream_handle(stream)))
+    out = {"counts": counts, "steps_run": sr}
+    if fs is not None:
+        out["final_state"] = fs
     return out
 
 
