@@ -58,6 +58,7 @@ __device__ __forceinline__ uint32_t lanes_u_less(uint32_t M, uint64_t thr, uint3
     if (thr >= TWO32) return M;
     const uint32_t th = (uint32_t)thr;
     uint32_t lt = 0u, eq = M;
+#pragma unroll 1
     for (uint32_t m = 0; m < 8u && eq; ++m) {
         const uint4 P = philox4x32_10(make_uint4(a, t, g, (tag << 8) | m), k0, k1);
         const uint32_t p[4] = {P.x, P.y, P.z, P.w};

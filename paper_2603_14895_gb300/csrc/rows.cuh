@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
     if (nrows == 0) return;
     const int nl = A.Wn * 32;
     const bool lanes_on = A.lane_cnt != nullptr;
+    const bool build = list_wanted(A);
     if (lanes_on)
         for (int i = threadIdx.x; i < 2 * nl; i += blockDim.x) s_lane[i] = 0;
     set_acc_zero(s_pc, A.S);
@@ -145,6 +146,14 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
     const int list_slot = A.k & 1;
     const int64_t nitems = nrows * A.nslices;
     Accum acc;
+    // The word contexts and the plane popcount changes belong to the thread's current
+    // slice: recomputed / flushed to shared memory only when the slice changes (never,
+    // when a row is a single slice).
+    int ctx_slice = -1;
+    WordCtx x[V];
+    int32_t d0[V], d1[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) d0[i] = d1[i] = 0;
 
     for (int64_t base = gwarp * RPI; base < nitems; base += nwarps * RPI) {
         const int64_t item = WARP_ROW ? base : base + team;
@@ -154,11 +163,14 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
         const int32_t v = has_row ? __ldg(rows + ridx) : 0;
         const int w0 = slice * SW + tl * V;
         const size_t off = (size_t)v * A.Wn + w0;
-        WordCtx x[V];
+        if (slice != ctx_slice) {
 #pragma unroll
-        for (int i = 0; i < V; ++i) {
-            x[i] = word_ctx(A, w0 + i);
-            if (!has_row) x[i].vm = 0u;
+            for (int i = 0; i < V; ++i) {
+                if (ctx_slice >= 0) set_acc_add(s_pc, x[i].s, d0[i], d1[i]);
+                d0[i] = d1[i] = 0;
+                x[i] = word_ctx(A, w0 + i);
+            }
+            ctx_slice = slice;
         }
         // lanes that can change through their in-arcs: S (SIR/SIS) or inactive (IC/LT)
         uint32_t need[V];
@@ -167,8 +179,10 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
             Vec<V> b{};
             if (MODEL == FSGP_SIR && has_row) b = ldg_vec<V>(A.cur + A.plane_words + off);
 #pragma unroll
-            for (int i = 0; i < V; ++i)
-                need[i] = MODEL == FSGP_SIR ? (x[i].vm & ~a.w[i] & ~b.w[i]) : (x[i].vm & ~a.w[i]);
+            for (int i = 0; i < V; ++i) {
+                const uint32_t vm = has_row ? x[i].vm : 0u;
+                need[i] = MODEL == FSGP_SIR ? (vm & ~a.w[i] & ~b.w[i]) : (vm & ~a.w[i]);
+            }
         }
         uint32_t any_need = 0u;
 #pragma unroll
@@ -245,8 +259,8 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
                 }
                 n0[i] = o.n0;
                 n1[i] = o.n1;
-                set_acc_add(s_pc, x[i].s, (long long)__popc(o.n0) - __popc(s0[i]),
-                            (long long)__popc(o.n1) - __popc(s1[i]));
+                d0[i] += __popc(o.n0) - __popc(s0[i]);
+                d1[i] += __popc(o.n1) - __popc(s1[i]);
                 if (lanes_on) {
                     lane_deltas(s_lane, w0 + i, s0[i], o.n0);
                     if (P == 2) lane_deltas(s_lane + nl, w0 + i, s1[i], o.n1);
@@ -263,8 +277,12 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
         const bool want = leader && fl != 0u;
         if (want && (fl & 1u)) acc.push_deg += (unsigned long long)(__ldg(A.out_ptr + v + 1) - __ldg(A.out_ptr + v));
         if (A.prof_bytes && leader) acc.bytes += row_bytes(SW, P, any_need != 0u, end - beg);
-        list_append(A, want, (int32_t)((uint32_t)v | ((fl & 1u) ? kPushBit : 0u)), list_slot);
+        list_append(A, build, want, (int32_t)((uint32_t)v | ((fl & 1u) ? kPushBit : 0u)), list_slot);
         if (sparse && leader) atomicAnd(&A.bitmap[v >> 5], ~(1u << (v & 31)));
+    }
+    if (ctx_slice >= 0) {
+#pragma unroll
+        for (int i = 0; i < V; ++i) set_acc_add(s_pc, x[i].s, d0[i], d1[i]);
     }
     flush_accum(A, acc, list_slot, WARP_ROW ? PK_MID : PK_SMALL);
     set_acc_flush(A, s_pc);
@@ -403,6 +421,7 @@ __global__ void __launch_bounds__(kBlock) k_hub_finalize(StepArgs A) {
     const bool sparse = *(volatile const int32_t *)&C->sparse != 0;
     const int nl = A.Wn * 32;
     const bool lanes_on = A.lane_cnt != nullptr;
+    const bool build = list_wanted(A);
     if (lanes_on)
         for (int i = threadIdx.x; i < 2 * nl; i += blockDim.x) s_lane[i] = 0;
     set_acc_zero(s_pc, A.S);
@@ -476,7 +495,7 @@ __global__ void __launch_bounds__(kBlock) k_hub_finalize(StepArgs A) {
         if (want && (fl & 1u)) acc.push_deg += (unsigned long long)(__ldg(A.out_ptr + v + 1) - __ldg(A.out_ptr + v));
         if (A.prof_bytes && cand && lane == 0)
             acc.bytes += row_bytes(A.Wn, P, false, 0) + 2ull * 4ull * 32ull * (unsigned long long)A.Wn;
-        list_append(A, want, (int32_t)((uint32_t)v | ((fl & 1u) ? kPushBit : 0u)), list_slot);
+        list_append(A, build, want, (int32_t)((uint32_t)v | ((fl & 1u) ? kPushBit : 0u)), list_slot);
         if (sparse && cand && lane == 0) atomicAnd(&A.bitmap[v >> 5], ~(1u << (v & 31)));
     }
     flush_accum(A, acc, list_slot, PK_HUBFIN);
@@ -510,11 +529,13 @@ int launch_rows_vt(const StepArgs &A, const StepLaunch &L, cudaStream_t s) {
 }
 
 template <int MODEL, int V, int TEAM>
-void occupancy_vt(size_t smem, int *bps_rows, int *bps_hub) {
-    int a = 1, b = 1;
+void occupancy_vt(size_t smem, int *bps_rows, int *bps_mid, int *bps_hub) {
+    int a = 1, m = 1, b = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_rows<MODEL, V, TEAM, false>, kBlock, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k_rows<MODEL, V, TEAM, true>, kBlock, smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_hub_chunks<MODEL, V, TEAM>, kBlock, 0);
     *bps_rows = a < 1 ? 1 : a;
+    *bps_mid = m < 1 ? 1 : m;
     *bps_hub = b < 1 ? 1 : b;
 }
 
@@ -569,8 +590,8 @@ int launch_split_rows(const StepArgs &A, int V, int TEAM, int grid_chunks, int g
 }
 
 template <int MODEL>
-int occupancy_rows(int V, int TEAM, size_t smem, int *bps_rows, int *bps_hub) {
-#define FSGP_O(v_, t_) occupancy_vt<MODEL, v_, t_>(smem, bps_rows, bps_hub)
+int occupancy_rows(int V, int TEAM, size_t smem, int *bps_rows, int *bps_mid, int *bps_hub) {
+#define FSGP_O(v_, t_) occupancy_vt<MODEL, v_, t_>(smem, bps_rows, bps_mid, bps_hub)
     FSGP_VT_SWITCH(FSGP_O)
 #undef FSGP_O
     return FSGP_OK;

@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(kBlock) k_init_scan(StepArgs A, int model) {
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     Accum acc;
     const bool two = model != FSGP_SIS;
+    const bool build = list_wanted(A);
     for (int64_t base = gwarp * 32; base < A.n; base += nwarps * 32) {
         const int64_t v = base + lane;
         const bool has = v < A.n;
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(kBlock) k_init_scan(StepArgs A, int model) {
         }
         if (push) acc.push_deg += (unsigned long long)(A.out_ptr[v + 1] - A.out_ptr[v]);
         if (has && A.prof_bytes) acc.bytes += (two ? 2ull : 1ull) * 4ull * (unsigned long long)A.Wn;
-        list_append(A, has && push, (int32_t)((uint32_t)v | kPushBit), 0);
+        list_append(A, build, has && push, (int32_t)((uint32_t)v | kPushBit), 0);
     }
     flush_accum(A, acc, 0, PK_INIT);
     set_acc_flush(A, s_pc);
@@ -373,12 +374,12 @@ static int launch_rows_model(int model, const StepArgs &A, const StepLaunch &L, 
     }
 }
 
-static int occupancy_model(int model, int V, int TEAM, size_t smem, int *a, int *b) {
+static int occupancy_model(int model, int V, int TEAM, size_t smem, int *a, int *m, int *b) {
     switch (model) {
-        case FSGP_SIR: return occupancy_rows<FSGP_SIR>(V, TEAM, smem, a, b);
-        case FSGP_SIS: return occupancy_rows<FSGP_SIS>(V, TEAM, smem, a, b);
-        case FSGP_IC: return occupancy_rows<FSGP_IC>(V, TEAM, smem, a, b);
-        default: return occupancy_rows<FSGP_LT>(V, TEAM, smem, a, b);
+        case FSGP_SIR: return occupancy_rows<FSGP_SIR>(V, TEAM, smem, a, m, b);
+        case FSGP_SIS: return occupancy_rows<FSGP_SIS>(V, TEAM, smem, a, m, b);
+        case FSGP_IC: return occupancy_rows<FSGP_IC>(V, TEAM, smem, a, m, b);
+        default: return occupancy_rows<FSGP_LT>(V, TEAM, smem, a, m, b);
     }
 }
 
@@ -554,8 +555,8 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     // ---------------------------------------------------------------- launch shape
     const size_t smem_lanes = want_lanes ? 2 * (size_t)Wn * 32 * sizeof(int32_t) : 0;
     if (smem_lanes > 32 * 1024) return fail(FSGP_EINVAL, "per-lane counters exceed shared memory");
-    int bps_rows = 1, bps_hub = 1;
-    rc = occupancy_model(model, V, TEAM, smem_lanes, &bps_rows, &bps_hub);
+    int bps_rows = 1, bps_mid = 1, bps_hub = 1;   // resident CTAs per SM of each kernel
+    rc = occupancy_model(model, V, TEAM, smem_lanes, &bps_rows, &bps_mid, &bps_hub);
     if (rc) return rc;
     Prof prof;
     const bool profiling = opt.profile != nullptr;
@@ -572,7 +573,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     const int per_block_small = (kBlock / 32) * (32 / TEAM);
     L.grid_small = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * bps_rows,
                                                                (items_small + per_block_small - 1) / per_block_small));
-    L.grid_mid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * bps_rows,
+    L.grid_mid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * bps_mid,
                                                              (items_mid + (kBlock / 32) - 1) / (kBlock / 32)));
     L.grid_hub = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * bps_hub,
                                                              g->hub.n_chunks * nslices));

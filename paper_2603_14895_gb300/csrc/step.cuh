@@ -262,15 +262,34 @@ __device__ __forceinline__ uint32_t min_count(const uint32_t (&c)[B], uint32_t M
 // lane's count.  thr is monotone in k, so every threshold lies between thr(kmin) and
 // thr(kmax) and shares their common binary prefix of L bits: all lanes are first
 // compared with that prefix together, and only lanes still tied after it are resolved
-// group by group (equal k) from bit L on.  The first 8 Philox planes (two blocks) are
-// generated once, on first use; deeper planes are generated where needed.
+// group by group (equal k) from bit L on.  Planes come in Philox blocks of four; the
+// first two blocks are kept in registers once generated, deeper blocks are generated
+// where needed.  The loops run over blocks and are not unrolled, to keep the kernels'
+// instruction footprint small.
 template <int B, class ThrFn>
 __device__ __forceinline__ uint32_t grouped_u_less(const uint32_t (&c)[B], uint32_t rem,
                                                    ThrFn thr_of, uint32_t a, uint32_t t,
                                                    uint32_t g, uint32_t tag, uint32_t k0,
                                                    uint32_t k1) {
-    uint32_t P[8];
-    int ngen = 0;
+    uint4 P0 = make_uint4(0u, 0u, 0u, 0u), P1 = P0;
+    bool have0 = false, have1 = false;
+    auto block = [&](uint32_t m) -> uint4 {
+        if (m == 0u) {
+            if (!have0) {
+                P0 = philox4x32_10(make_uint4(a, t, g, tag << 8), k0, k1);
+                have0 = true;
+            }
+            return P0;
+        }
+        if (m == 1u) {
+            if (!have1) {
+                P1 = philox4x32_10(make_uint4(a, t, g, (tag << 8) | 1u), k0, k1);
+                have1 = true;
+            }
+            return P1;
+        }
+        return philox4x32_10(make_uint4(a, t, g, (tag << 8) | m), k0, k1);
+    };
     uint32_t res = 0u;
     int L = 0;
     uint32_t eq = rem;
@@ -282,28 +301,21 @@ __device__ __forceinline__ uint32_t grouped_u_less(const uint32_t (&c)[B], uint3
             L = x ? __clz(x) : 32;
             const uint32_t th = (uint32_t)ta;
             uint32_t lt = 0u;
-            uint4 Q = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll 1
+            for (int m = 0; m * 4 < L && eq; ++m) {
+                const uint4 Q = block((uint32_t)m);
+                const uint32_t q[4] = {Q.x, Q.y, Q.z, Q.w};
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                if (j >= L || !eq) break;
-                uint32_t p;
-                if (j < 8) {
-                    if ((j & 3) == 0 && ngen <= (j >> 2)) {
-                        const uint4 R = philox4x32_10(make_uint4(a, t, g, (tag << 8) | (uint32_t)(j >> 2)), k0, k1);
-                        P[j] = R.x; P[j + 1] = R.y; P[j + 2] = R.z; P[j + 3] = R.w;
-                        ngen = (j >> 2) + 1;
-                    }
-                    p = P[j];
-                } else {
-                    if ((j & 3) == 0) Q = philox4x32_10(make_uint4(a, t, g, (tag << 8) | (uint32_t)(j >> 2)), k0, k1);
-                    p = (j & 3) == 0 ? Q.x : (j & 3) == 1 ? Q.y : (j & 3) == 2 ? Q.z : Q.w;
+                for (int i = 0; i < 4; ++i) {
+                    const int j = m * 4 + i;
+                    if (j < L) FSGP_BIT_STEP(q[i], (th >> (31 - j)) & 1u, lt, eq);
                 }
-                FSGP_BIT_STEP(p, (th >> (31 - j)) & 1u, lt, eq);
             }
             res = lt;
             if (L == 32) return res;   // equal thresholds: lanes still tied have u == thr
         }
     }
+#pragma unroll 1
     while (eq) {
         const uint32_t k = lane_count<B>(c, __ffs(eq) - 1);
         const uint32_t M = lanes_with_count<B>(c, eq, k);
@@ -316,25 +328,15 @@ __device__ __forceinline__ uint32_t grouped_u_less(const uint32_t (&c)[B], uint3
         }
         const uint32_t th = (uint32_t)thr;
         uint32_t lt = 0u, e2 = M;
-        uint4 Q = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll 1
+        for (int m = L >> 2; m < 8 && e2; ++m) {
+            const uint4 Q = block((uint32_t)m);
+            const uint32_t q[4] = {Q.x, Q.y, Q.z, Q.w};
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            if (j < L) continue;
-            if (!e2) break;
-            uint32_t p;
-            if (j < 8) {
-                if (ngen <= (j >> 2)) {
-                    const int jb = j & ~3;
-                    const uint4 R = philox4x32_10(make_uint4(a, t, g, (tag << 8) | (uint32_t)(j >> 2)), k0, k1);
-                    P[jb] = R.x; P[jb + 1] = R.y; P[jb + 2] = R.z; P[jb + 3] = R.w;
-                    ngen = (j >> 2) + 1;
-                }
-                p = P[j];
-            } else {
-                if ((j & 3) == 0 || j == L) Q = philox4x32_10(make_uint4(a, t, g, (tag << 8) | (uint32_t)(j >> 2)), k0, k1);
-                p = (j & 3) == 0 ? Q.x : (j & 3) == 1 ? Q.y : (j & 3) == 2 ? Q.z : Q.w;
+            for (int i = 0; i < 4; ++i) {
+                const int j = m * 4 + i;
+                if (j >= L) FSGP_BIT_STEP(q[i], (th >> (31 - j)) & 1u, lt, e2);
             }
-            FSGP_BIT_STEP(p, (th >> (31 - j)) & 1u, lt, e2);
         }
         res |= lt;
     }
@@ -476,10 +478,16 @@ __device__ __forceinline__ void flush_lanes(const StepArgs &A, int32_t *s_lane, 
     }
 }
 
-// Warp-aggregated append of flagged rows to the next step's list.
-__device__ __forceinline__ void list_append(const StepArgs &A, bool want, int32_t entry,
+// Whether this step lists its rows for the next one (set by the step control kernel
+// before the row kernels; read once per kernel).
+__device__ __forceinline__ bool list_wanted(const StepArgs &A) {
+    return *(volatile const int32_t *)&A.ctl->build_list != 0;
+}
+
+// Warp-aggregated append of flagged rows to the next step's list (build = list_wanted).
+__device__ __forceinline__ void list_append(const StepArgs &A, bool build, bool want, int32_t entry,
                                             int list_slot) {
-    if (!*(volatile const int32_t *)&A.ctl->build_list) return;   // uniform per launch
+    if (!build) return;   // uniform per launch
     const unsigned m = __ballot_sync(0xffffffffu, want);
     if (!m) return;
     const int lane = threadIdx.x & 31;
@@ -540,7 +548,7 @@ int run_sets(fsgp_graph *g, int model, int ic_mode, const SetSpec *sets, int n_s
 template <int MODEL>
 int launch_rows(const StepArgs &A, const StepLaunch &L, cudaStream_t s);
 template <int MODEL>
-int occupancy_rows(int V, int TEAM, size_t smem, int *bps_rows, int *bps_hub);
+int occupancy_rows(int V, int TEAM, size_t smem, int *bps_rows, int *bps_mid, int *bps_hub);
 template <int MODEL>
 int launch_split_rows(const StepArgs &A, int V, int TEAM, int grid_chunks, int grid_fin,
                       cudaStream_t s);
