@@ -503,6 +503,134 @@ __global__ void __launch_bounds__(kBlock) k_hub_finalize(StepArgs A) {
     if (lanes_on) flush_lanes(A, s_lane, nl);
 }
 
+// Rows without in-arcs, dense steps only (on frontier steps such rows come through the
+// candidate lists of k_rows): nothing to gather, so a lane changes only by recovery
+// (SIR/SIS) or by the newly-active plane clearing (IC/LT) -- the update of k_rows with
+// all counts zero.  One team per (row, slice) item; the next item's row id and state
+// words are loaded one item ahead, which the missing counters leave registers for.
+template <int MODEL, int V, int TEAM>
+__global__ void __launch_bounds__(kBlock) k_static_rows(StepArgs A) {
+    extern __shared__ int32_t s_lane[];
+    __shared__ unsigned long long s_pc[2 * kMaxSets];
+    constexpr int TPW = 32 / TEAM;
+    constexpr int SW = TEAM * V;
+    constexpr int P = ModelTraits<MODEL>::planes;
+    const Ctl *C = A.ctl;
+    if (*(volatile const int32_t *)&C->stop) return;
+    if (*(volatile const int32_t *)&C->sparse) return;
+    const int64_t nitems = (int64_t)A.n_zero * A.nslices;
+    if (nitems == 0) return;
+    const int nl = A.Wn * 32;
+    const bool lanes_on = A.lane_cnt != nullptr;
+    const bool build = list_wanted(A);
+    if (lanes_on)
+        for (int i = threadIdx.x; i < 2 * nl; i += blockDim.x) s_lane[i] = 0;
+    set_acc_zero(s_pc, A.S);
+    const int lane = threadIdx.x & 31;
+    const int team = lane / TEAM;
+    const int tl = lane % TEAM;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int list_slot = A.k & 1;
+    const int64_t stride = nwarps * TPW;
+    Accum acc;
+    int ctx_slice = -1;
+    WordCtx x[V];
+    int32_t d0[V], d1[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) d0[i] = d1[i] = 0;
+    // item -> (row id, slice, own words), loaded one item ahead
+    auto fetch = [&](int64_t it, int32_t &v, int &slice, uint32_t (&a)[V], uint32_t (&b)[V]) {
+        v = 0;
+        slice = 0;
+#pragma unroll
+        for (int i = 0; i < V; ++i) a[i] = b[i] = 0u;
+        if (it < nitems) {
+            const int64_t r = it / A.nslices;
+            slice = (int)(it - r * A.nslices);
+            v = __ldg(A.rows_zero + r);
+            const size_t off = (size_t)v * A.Wn + slice * SW + tl * V;
+            const Vec<V> va = ldg_vec<V>(A.cur + off);
+#pragma unroll
+            for (int i = 0; i < V; ++i) a[i] = va.w[i];
+            if (P == 2) {
+                const Vec<V> vb = ldg_vec<V>(A.cur + A.plane_words + off);
+#pragma unroll
+                for (int i = 0; i < V; ++i) b[i] = vb.w[i];
+            }
+        }
+    };
+    int64_t item = gwarp * TPW + team;
+    int32_t v_nx;
+    int slice_nx;
+    uint32_t a_nx[V], b_nx[V];
+    fetch(item, v_nx, slice_nx, a_nx, b_nx);
+    for (int64_t base = gwarp * TPW; base < nitems; base += stride, item += stride) {
+        const bool has_row = item < nitems;
+        const int32_t v = v_nx;
+        const int slice = slice_nx;
+        uint32_t s0[V], s1[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            s0[i] = a_nx[i];
+            s1[i] = b_nx[i];
+        }
+        fetch(item + stride, v_nx, slice_nx, a_nx, b_nx);
+        const int w0 = slice * SW + tl * V;
+        if (has_row && slice != ctx_slice) {
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                if (ctx_slice >= 0) set_acc_add(s_pc, x[i].s, d0[i], d1[i]);
+                d0[i] = d1[i] = 0;
+                x[i] = word_ctx(A, w0 + i);
+            }
+            ctx_slice = slice;
+        }
+        uint32_t fl = 0u;
+        if (has_row) {
+            uint32_t n0[V], n1[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SIS) {
+                    const SetParams &p = A.sp[x[i].s];
+                    const uint32_t rec = lanes_u_less(s0[i] & x[i].vm, __ldg(&p.g_rec), (uint32_t)v, A.t,
+                                                      x[i].g, TAG_RECOVER, x[i].k0, x[i].k1);
+                    n0[i] = s0[i] & ~rec;
+                    n1[i] = MODEL == FSGP_SIR ? (s1[i] | rec) : 0u;
+                } else {
+                    n0[i] = s0[i];
+                    n1[i] = 0u;
+                }
+                d0[i] += __popc(n0[i]) - __popc(s0[i]);
+                d1[i] += __popc(n1[i]) - __popc(s1[i]);
+                if (lanes_on) {
+                    lane_deltas(s_lane, w0 + i, s0[i], n0[i]);
+                    if (P == 2) lane_deltas(s_lane + nl, w0 + i, s1[i], n1[i]);
+                }
+                if (n0[i] != s0[i] || n1[i] != s1[i]) fl |= 2u;
+                if ((MODEL == FSGP_SIR || MODEL == FSGP_SIS) ? (n0[i] != 0u) : (n1[i] != 0u)) fl |= 1u;
+            }
+            const size_t off = (size_t)v * A.Wn + w0;
+            st_vec<V>(A.nxt + off, n0);
+            if (P == 2) st_vec<V>(A.nxt + A.plane_words + off, n1);
+        }
+#pragma unroll
+        for (int o = 1; o < TEAM; o <<= 1) fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+        const bool leader = has_row && tl == 0;
+        const bool want = leader && fl != 0u;
+        if (want && (fl & 1u)) acc.push_deg += (unsigned long long)(__ldg(A.out_ptr + v + 1) - __ldg(A.out_ptr + v));
+        if (A.prof_bytes && leader) acc.bytes += row_bytes(SW, P, false, 0);
+        list_append(A, build, want, (int32_t)((uint32_t)v | ((fl & 1u) ? kPushBit : 0u)), list_slot);
+    }
+    if (ctx_slice >= 0) {
+#pragma unroll
+        for (int i = 0; i < V; ++i) set_acc_add(s_pc, x[i].s, d0[i], d1[i]);
+    }
+    flush_accum(A, acc, list_slot, PK_SMALL);
+    set_acc_flush(A, s_pc);
+    if (lanes_on) flush_lanes(A, s_lane, nl);
+}
+
 // ------------------------------------------------------------------------- launch
 
 template <int MODEL, int V, int TEAM>
@@ -525,12 +653,19 @@ int launch_rows_vt(const StepArgs &A, const StepLaunch &L, cudaStream_t s) {
         k_rows<MODEL, V, TEAM, false><<<L.grid_small, kBlock, L.smem_lanes, s>>>(A, 0);
         if (pr) pr->stop(s);
     }
+    if (L.have_zero) {
+        if (pr) pr->start(PK_SMALL, s);
+        k_static_rows<MODEL, V, TEAM><<<L.grid_zero, kBlock, L.smem_lanes, s>>>(A);
+        if (pr) pr->stop(s);
+    }
     return FSGP_OK;
 }
 
 template <int MODEL, int V, int TEAM>
-void occupancy_vt(size_t smem, int *bps_rows, int *bps_mid, int *bps_hub) {
-    int a = 1, m = 1, b = 1;
+void occupancy_vt(size_t smem, int *bps_rows, int *bps_mid, int *bps_hub, int *bps_zero) {
+    int a = 1, m = 1, b = 1, z = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&z, k_static_rows<MODEL, V, TEAM>, kBlock, smem);
+    *bps_zero = z < 1 ? 1 : z;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_rows<MODEL, V, TEAM, false>, kBlock, smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k_rows<MODEL, V, TEAM, true>, kBlock, smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_hub_chunks<MODEL, V, TEAM>, kBlock, 0);
@@ -590,8 +725,9 @@ int launch_split_rows(const StepArgs &A, int V, int TEAM, int grid_chunks, int g
 }
 
 template <int MODEL>
-int occupancy_rows(int V, int TEAM, size_t smem, int *bps_rows, int *bps_mid, int *bps_hub) {
-#define FSGP_O(v_, t_) occupancy_vt<MODEL, v_, t_>(smem, bps_rows, bps_mid, bps_hub)
+int occupancy_rows(int V, int TEAM, size_t smem, int *bps_rows, int *bps_mid, int *bps_hub,
+                   int *bps_zero) {
+#define FSGP_O(v_, t_) occupancy_vt<MODEL, v_, t_>(smem, bps_rows, bps_mid, bps_hub, bps_zero)
     FSGP_VT_SWITCH(FSGP_O)
 #undef FSGP_O
     return FSGP_OK;

@@ -85,9 +85,10 @@ struct StepArgs {
     unsigned long long *pc;        // [S][2] plane popcounts of this step (running totals)
     int32_t *lane_cnt;             // [2][Wn*32] running per-lane plane counts, or null
     // row lists
-    const int32_t *__restrict__ rows_small;
+    const int32_t *__restrict__ rows_small;   // dense steps: small rows with in-arcs
     const int32_t *__restrict__ rows_mid;
-    int32_t n_small, n_mid;
+    const int32_t *__restrict__ rows_zero;    // dense steps: rows without in-arcs
+    int32_t n_small, n_mid, n_zero;
     int32_t *cand_small;
     int32_t *cand_mid;
     uint32_t *bitmap;
@@ -501,9 +502,9 @@ __device__ __forceinline__ void list_append(const StepArgs &A, bool build, bool 
 // Launch shape of the row kernels of one step (host side).
 struct StepLaunch {
     int V, TEAM;           // words per thread, threads per slice team
-    int grid_small, grid_mid, grid_hub, grid_fin;
+    int grid_small, grid_mid, grid_hub, grid_fin, grid_zero;
     size_t smem_lanes;     // dynamic shared memory for per-lane counters (0 = off)
-    bool have_small, have_mid, have_hub;
+    bool have_small, have_mid, have_hub, have_zero;
     struct Prof *prof;     // host-side event recorder, or null
 };
 
@@ -548,7 +549,8 @@ int run_sets(fsgp_graph *g, int model, int ic_mode, const SetSpec *sets, int n_s
 template <int MODEL>
 int launch_rows(const StepArgs &A, const StepLaunch &L, cudaStream_t s);
 template <int MODEL>
-int occupancy_rows(int V, int TEAM, size_t smem, int *bps_rows, int *bps_mid, int *bps_hub);
+int occupancy_rows(int V, int TEAM, size_t smem, int *bps_rows, int *bps_mid, int *bps_hub,
+                   int *bps_zero);
 template <int MODEL>
 int launch_split_rows(const StepArgs &A, int V, int TEAM, int grid_chunks, int grid_fin,
                       cudaStream_t s);
