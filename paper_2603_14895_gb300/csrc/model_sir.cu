@@ -4,6 +4,6 @@
 
 namespace fsgp {
 template int launch_rows<FSGP_SIR>(const StepArgs &, const StepLaunch &, cudaStream_t);
-template int occupancy_rows<FSGP_SIR>(int, int, size_t, int *, int *, int *, int *);
+template int occupancy_rows<FSGP_SIR>(int, int, size_t, RowOccupancy *);
 template int launch_split_rows<FSGP_SIR>(const StepArgs &, int, int, int, int, cudaStream_t);
 }  // namespace fsgp

@@ -109,12 +109,16 @@ constexpr int min_ctas() { return V == 4 ? 2 : (V == 2 ? (WIDE ? 3 : 4) : 4); }
 
 // Row kernel: one work item is one slice (TEAM*V words) of one row.
 // WARP_ROW = false: one team per item; true: one warp per item.
-// which: 0 = small rows, 1 = mid rows.
-template <int MODEL, int V, int TEAM, bool WARP_ROW>
+// BT: counter bits of a team kernel, sized to its rows' in-degree bound (fewer planes =
+// fewer registers and cheaper counting and grouping).
+// which: 0 = small rows with 16..small_max in-arcs (and every small row of a frontier
+// step), 1 = mid rows, 2 = rows with 1..3 in-arcs, 3 = rows with 4..15 in-arcs (2 and 3:
+// dense steps only).
+template <int MODEL, int V, int TEAM, bool WARP_ROW, int BT = kSmallBits>
 __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepArgs A, int which) {
     extern __shared__ int32_t s_lane[];
     __shared__ unsigned long long s_pc[2 * kMaxSets];
-    constexpr int B = WARP_ROW ? kWideBits : kSmallBits;
+    constexpr int B = WARP_ROW ? kWideBits : BT;
     constexpr int TPW = 32 / TEAM;
     constexpr int SW = TEAM * V;
     constexpr int P = ModelTraits<MODEL>::planes;
@@ -124,11 +128,12 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
     const int32_t *rows;
     int64_t nrows;
     if (sparse) {
+        if (which >= 2) return;
         rows = which ? A.cand_mid : A.cand_small;
         nrows = (int64_t)((volatile const uint32_t *)C->cand_n)[which];
     } else {
-        rows = which ? A.rows_mid : A.rows_small;
-        nrows = which ? A.n_mid : A.n_small;
+        rows = which == 0 ? A.rows_small : which == 1 ? A.rows_mid : which == 2 ? A.rows_tiny : A.rows_small4;
+        nrows = which == 0 ? A.n_small : which == 1 ? A.n_mid : which == 2 ? A.n_tiny : A.n_small4;
     }
     if (nrows == 0) return;
     const int nl = A.Wn * 32;
@@ -250,7 +255,7 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
             for (int i = 0; i < V; ++i) {
                 WordOut o;
                 if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SIS) {
-                    o = update_sir_word<MODEL, B>(A, (uint32_t)v, x[i], s0[i], s1[i], c[i]);
+                    o = update_sir_word<MODEL, B>(A, (uint32_t)v, x[i], s0[i], s1[i], end - beg, c[i]);
                 } else if constexpr (MODEL == FSGP_IC) {
                     o.n0 = s0[i] | newly[i];
                     o.n1 = newly[i];
@@ -468,7 +473,7 @@ __global__ void __launch_bounds__(kBlock) k_hub_finalize(StepArgs A) {
                     const WordCtx x = word_ctx(A, w);
                     WordOut o;
                     if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SIS) {
-                        o = update_sir_word<MODEL, 32>(A, (uint32_t)v, x, s0, s1, c);
+                        o = update_sir_word<MODEL, 32>(A, (uint32_t)v, x, s0, s1, d, c);
                     } else if constexpr (MODEL == FSGP_IC) {
                         const uint32_t nw2 = newly & x.vm & ~s0;
                         o.n0 = s0 | nw2;
@@ -653,6 +658,16 @@ int launch_rows_vt(const StepArgs &A, const StepLaunch &L, cudaStream_t s) {
         k_rows<MODEL, V, TEAM, false><<<L.grid_small, kBlock, L.smem_lanes, s>>>(A, 0);
         if (pr) pr->stop(s);
     }
+    if (L.have_small4) {
+        if (pr) pr->start(PK_SMALL, s);
+        k_rows<MODEL, V, TEAM, false, 4><<<L.grid_small4, kBlock, L.smem_lanes, s>>>(A, 3);
+        if (pr) pr->stop(s);
+    }
+    if (L.have_tiny) {
+        if (pr) pr->start(PK_SMALL, s);
+        k_rows<MODEL, V, TEAM, false, 2><<<L.grid_tiny, kBlock, L.smem_lanes, s>>>(A, 2);
+        if (pr) pr->stop(s);
+    }
     if (L.have_zero) {
         if (pr) pr->start(PK_SMALL, s);
         k_static_rows<MODEL, V, TEAM><<<L.grid_zero, kBlock, L.smem_lanes, s>>>(A);
@@ -662,16 +677,20 @@ int launch_rows_vt(const StepArgs &A, const StepLaunch &L, cudaStream_t s) {
 }
 
 template <int MODEL, int V, int TEAM>
-void occupancy_vt(size_t smem, int *bps_rows, int *bps_mid, int *bps_hub, int *bps_zero) {
-    int a = 1, m = 1, b = 1, z = 1;
+void occupancy_vt(size_t smem, RowOccupancy *o) {
+    int a = 1, m = 1, b = 1, z = 1, s4 = 1, s2 = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&z, k_static_rows<MODEL, V, TEAM>, kBlock, smem);
-    *bps_zero = z < 1 ? 1 : z;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s4, k_rows<MODEL, V, TEAM, false, 4>, kBlock, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s2, k_rows<MODEL, V, TEAM, false, 2>, kBlock, smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_rows<MODEL, V, TEAM, false>, kBlock, smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k_rows<MODEL, V, TEAM, true>, kBlock, smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_hub_chunks<MODEL, V, TEAM>, kBlock, 0);
-    *bps_rows = a < 1 ? 1 : a;
-    *bps_mid = m < 1 ? 1 : m;
-    *bps_hub = b < 1 ? 1 : b;
+    o->small = a < 1 ? 1 : a;
+    o->mid = m < 1 ? 1 : m;
+    o->hub = b < 1 ? 1 : b;
+    o->zero = z < 1 ? 1 : z;
+    o->small4 = s4 < 1 ? 1 : s4;
+    o->tiny = s2 < 1 ? 1 : s2;
 }
 
 #define FSGP_VT_SWITCH(MACRO)                          \
@@ -725,9 +744,8 @@ int launch_split_rows(const StepArgs &A, int V, int TEAM, int grid_chunks, int g
 }
 
 template <int MODEL>
-int occupancy_rows(int V, int TEAM, size_t smem, int *bps_rows, int *bps_mid, int *bps_hub,
-                   int *bps_zero) {
-#define FSGP_O(v_, t_) occupancy_vt<MODEL, v_, t_>(smem, bps_rows, bps_mid, bps_hub, bps_zero)
+int occupancy_rows(int V, int TEAM, size_t smem, RowOccupancy *o) {
+#define FSGP_O(v_, t_) occupancy_vt<MODEL, v_, t_>(smem, o)
     FSGP_VT_SWITCH(FSGP_O)
 #undef FSGP_O
     return FSGP_OK;

@@ -374,12 +374,12 @@ static int launch_rows_model(int model, const StepArgs &A, const StepLaunch &L, 
     }
 }
 
-static int occupancy_model(int model, int V, int TEAM, size_t smem, int *a, int *m, int *b, int *z) {
+static int occupancy_model(int model, int V, int TEAM, size_t smem, RowOccupancy *o) {
     switch (model) {
-        case FSGP_SIR: return occupancy_rows<FSGP_SIR>(V, TEAM, smem, a, m, b, z);
-        case FSGP_SIS: return occupancy_rows<FSGP_SIS>(V, TEAM, smem, a, m, b, z);
-        case FSGP_IC: return occupancy_rows<FSGP_IC>(V, TEAM, smem, a, m, b, z);
-        default: return occupancy_rows<FSGP_LT>(V, TEAM, smem, a, m, b, z);
+        case FSGP_SIR: return occupancy_rows<FSGP_SIR>(V, TEAM, smem, o);
+        case FSGP_SIS: return occupancy_rows<FSGP_SIS>(V, TEAM, smem, o);
+        case FSGP_IC: return occupancy_rows<FSGP_IC>(V, TEAM, smem, o);
+        default: return occupancy_rows<FSGP_LT>(V, TEAM, smem, o);
     }
 }
 
@@ -454,9 +454,16 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     const int32_t start_mid = bh >= 1 ? g->cls.bucket_start[bh - 1] : n;
     const int32_t start_small = g->cls.bucket_start[bs];
     const int32_t n_mid = start_small - start_mid;
-    const int32_t start_zero = g->cls.bucket_start[0];   // in-degree 0 rows come last
+    // small rows by in-degree class; rows_sorted holds the buckets in descending order
+    // (bucket b: 2^(b-1) <= d < 2^b, bucket 0: d = 0), so each class is one range
+    const int32_t start_zero = g->cls.bucket_start[0];
+    const int32_t start_tiny = bs >= 2 ? g->cls.bucket_start[2] : start_small;     // d 1..3
+    const int32_t start_small4 = bs >= 4 ? g->cls.bucket_start[4] : start_small;   // d 4..15
     const int32_t n_zero = n - start_zero;
-    const int32_t n_small = start_zero - start_small;
+    const int32_t n_tiny = start_zero - std::max(start_tiny, start_small);
+    const int32_t n_small4 = std::max(start_tiny, start_small) - std::max(start_small4, start_small);
+    const int32_t n_small = std::max(start_small4, start_small) - start_small;        // d 16..small_max
+    const int32_t n_small_all = n - start_small;
 
     // per-set parameters and survival tables
     std::vector<uint64_t> surv_all;
@@ -557,8 +564,8 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     // ---------------------------------------------------------------- launch shape
     const size_t smem_lanes = want_lanes ? 2 * (size_t)Wn * 32 * sizeof(int32_t) : 0;
     if (smem_lanes > 32 * 1024) return fail(FSGP_EINVAL, "per-lane counters exceed shared memory");
-    int bps_rows = 1, bps_mid = 1, bps_hub = 1, bps_zero = 1;   // resident CTAs per SM of each kernel
-    rc = occupancy_model(model, V, TEAM, smem_lanes, &bps_rows, &bps_mid, &bps_hub, &bps_zero);
+    RowOccupancy occ{};
+    rc = occupancy_model(model, V, TEAM, smem_lanes, &occ);
     if (rc) return rc;
     Prof prof;
     const bool profiling = opt.profile != nullptr;
@@ -567,24 +574,30 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     L.V = V;
     L.TEAM = TEAM;
     L.smem_lanes = smem_lanes;
-    // small rows on frontier steps (candidate lists) include the in-degree 0 rows
-    L.have_small = n_small + n_zero > 0;
+    // the 16..small_max kernel also takes every small row of a frontier step
+    L.have_small = n_small_all > 0;
+    L.have_small4 = n_small4 > 0;
+    L.have_tiny = n_tiny > 0;
     L.have_zero = n_zero > 0;
     L.have_mid = n_mid > 0;
     L.have_hub = n_hubs > 0;
     L.prof = profiling ? &prof : nullptr;
-    const int64_t items_small = ((int64_t)n_small + n_zero) * nslices, items_mid = (int64_t)n_mid * nslices;
+    const int64_t items_small = (int64_t)n_small_all * nslices, items_mid = (int64_t)n_mid * nslices;
     const int64_t items_zero = (int64_t)n_zero * nslices;
     const int per_block_small = (kBlock / 32) * (32 / TEAM);
-    L.grid_small = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * bps_rows,
-                                                               (items_small + per_block_small - 1) / per_block_small));
-    L.grid_mid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * bps_mid,
+    auto grid_for_items = [&](int per_sm, int64_t items) {
+        return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * per_sm,
+                                                           (items + per_block_small - 1) / per_block_small));
+    };
+    L.grid_small = grid_for_items(occ.small, items_small);
+    L.grid_small4 = grid_for_items(occ.small4, (int64_t)n_small4 * nslices);
+    L.grid_tiny = grid_for_items(occ.tiny, (int64_t)n_tiny * nslices);
+    L.grid_mid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * occ.mid,
                                                              (items_mid + (kBlock / 32) - 1) / (kBlock / 32)));
-    L.grid_hub = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * bps_hub,
+    L.grid_hub = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * occ.hub,
                                                              g->hub.n_chunks * nslices));
     L.grid_fin = (int)std::max<int64_t>(1, ((int64_t)n_hubs + (kBlock / 32) - 1) / (kBlock / 32));
-    L.grid_zero = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * bps_zero,
-                                                              (items_zero + per_block_small - 1) / per_block_small));
+    L.grid_zero = grid_for_items(occ.zero, items_zero);
     const int grid_mark = g->sm_count * 8;
     const int grid_scan = grid_cap((int64_t)n, kBlock, g->sm_count, 8);
 
@@ -608,8 +621,12 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     A.ctl = ctl;
     A.lane_cnt = want_lanes ? (int32_t *)(ws + off[O_LANES]) : nullptr;
     A.rows_small = g->rows_sorted + start_small;
+    A.rows_small4 = g->rows_sorted + std::max(start_small4, start_small);
+    A.rows_tiny = g->rows_sorted + std::max(start_tiny, start_small);
     A.rows_zero = g->rows_sorted + start_zero;
     A.n_zero = n_zero;
+    A.n_small4 = n_small4;
+    A.n_tiny = n_tiny;
     A.rows_mid = g->rows_sorted + start_mid;
     A.n_small = n_small;
     A.n_mid = n_mid;
@@ -706,7 +723,8 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
         rc = launch_rows_model(model, A, L, s);
         if (rc) return rc;
         launches += 1 + (allow_sparse ? 1 : 0) + (L.have_hub ? 2 : 0) + (L.have_mid ? 1 : 0) +
-                    (L.have_small ? 1 : 0) + (L.have_zero ? 1 : 0);
+                    (L.have_small ? 1 : 0) + (L.have_zero ? 1 : 0) + (L.have_small4 ? 1 : 0) +
+                    (L.have_tiny ? 1 : 0);
     }
     FSGP_CUDA(cudaGetLastError());
     if (profiling) prof.start(PK_RESULTS, s);

@@ -85,10 +85,13 @@ struct StepArgs {
     unsigned long long *pc;        // [S][2] plane popcounts of this step (running totals)
     int32_t *lane_cnt;             // [2][Wn*32] running per-lane plane counts, or null
     // row lists
-    const int32_t *__restrict__ rows_small;   // dense steps: small rows with in-arcs
+    // dense steps: small rows by in-degree class (16.., 4..15, 1..3, 0), mid rows
+    const int32_t *__restrict__ rows_small;
+    const int32_t *__restrict__ rows_small4;
+    const int32_t *__restrict__ rows_tiny;
+    const int32_t *__restrict__ rows_zero;
     const int32_t *__restrict__ rows_mid;
-    const int32_t *__restrict__ rows_zero;    // dense steps: rows without in-arcs
-    int32_t n_small, n_mid, n_zero;
+    int32_t n_small, n_small4, n_tiny, n_zero, n_mid;
     int32_t *cand_small;
     int32_t *cand_mid;
     uint32_t *bitmap;
@@ -154,9 +157,10 @@ __device__ __forceinline__ void add4(uint32_t (&c)[B], uint32_t x0, uint32_t x1,
     c[0] ^= s0;
     uint32_t t = c[1];
     c[1] = t ^ s1 ^ carry;
+    if constexpr (B == 2) return;   // counts below 4 (rows with at most 3 in-arcs)
     carry = (t & s1) | (carry & (t ^ s1));
-    t = c[2];
-    c[2] = t ^ s2 ^ carry;
+    t = c[B > 2 ? 2 : 1];
+    c[B > 2 ? 2 : 1] = t ^ s2 ^ carry;
     carry = (t & s2) | (carry & (t ^ s2));
 #pragma unroll
     for (int b = 3; b < B; ++b) {
@@ -259,19 +263,29 @@ __device__ __forceinline__ uint32_t min_count(const uint32_t (&c)[B], uint32_t M
         }                             \
     } while (0)
 
+// Highest counter plane set in any lane of M (-1 if none), branch-free.
+template <int B>
+__device__ __forceinline__ int top_plane(const uint32_t (&c)[B], uint32_t M) {
+    int hb = -1;
+#pragma unroll
+    for (int b = 0; b < B; ++b) hb = (M & c[b]) ? b : hb;
+    return hb;
+}
+
 // Lanes of `rem` whose uniform u(tag, a, t, lane) is below thr(k_lane), k_lane the
-// lane's count.  thr is monotone in k, so every threshold lies between thr(kmin) and
-// thr(kmax) and shares their common binary prefix of L bits: all lanes are first
+// lane's count, 1 <= k_lane <= kcap.  thr is monotone in k, so every threshold lies
+// between thr(1) and thr(khi), khi = min(kcap, 2^(hb+1) - 1) with hb the highest counter
+// plane in use, and shares their common binary prefix of L bits: all lanes are first
 // compared with that prefix together, and only lanes still tied after it are resolved
-// group by group (equal k) from bit L on.  Planes come in Philox blocks of four; the
-// first two blocks are kept in registers once generated, deeper blocks are generated
-// where needed.  The loops run over blocks and are not unrolled, to keep the kernels'
-// instruction footprint small.
+// group by group (equal k, counts read from the hb+1 planes in use) from bit L on.
+// Planes come in Philox blocks of four; the first two blocks are kept in registers once
+// generated, deeper blocks are generated where needed.  The loops run over blocks and
+// are not unrolled, to keep the kernels' instruction footprint small.
 template <int B, class ThrFn>
 __device__ __forceinline__ uint32_t grouped_u_less(const uint32_t (&c)[B], uint32_t rem,
-                                                   ThrFn thr_of, uint32_t a, uint32_t t,
-                                                   uint32_t g, uint32_t tag, uint32_t k0,
-                                                   uint32_t k1) {
+                                                   ThrFn thr_of, uint32_t kcap, uint32_t a,
+                                                   uint32_t t, uint32_t g, uint32_t tag,
+                                                   uint32_t k0, uint32_t k1) {
     uint4 P0 = make_uint4(0u, 0u, 0u, 0u), P1 = P0;
     bool have0 = false, have1 = false;
     auto block = [&](uint32_t m) -> uint4 {
@@ -291,12 +305,15 @@ __device__ __forceinline__ uint32_t grouped_u_less(const uint32_t (&c)[B], uint3
         }
         return philox4x32_10(make_uint4(a, t, g, (tag << 8) | m), k0, k1);
     };
+    const int nb = top_plane<B>(c, rem) + 1;    // rem lanes have k >= 1, so nb >= 1
+    uint32_t khi = nb >= 32 ? 0xffffffffu : (1u << nb) - 1u;
+    if (khi > kcap) khi = kcap;
     uint32_t res = 0u;
     int L = 0;
     uint32_t eq = rem;
     {
-        const uint64_t ta = thr_of(min_count<B>(c, rem));
-        const uint64_t tb = thr_of(max_count<B>(c, rem));
+        const uint64_t ta = thr_of(1u);
+        const uint64_t tb = thr_of(khi);
         if (ta > 0ull && ta < TWO32 && tb > 0ull && tb < TWO32) {
             const uint32_t x = (uint32_t)ta ^ (uint32_t)tb;
             L = x ? __clz(x) : 32;
@@ -318,8 +335,16 @@ __device__ __forceinline__ uint32_t grouped_u_less(const uint32_t (&c)[B], uint3
     }
 #pragma unroll 1
     while (eq) {
-        const uint32_t k = lane_count<B>(c, __ffs(eq) - 1);
-        const uint32_t M = lanes_with_count<B>(c, eq, k);
+        const int l0 = __ffs(eq) - 1;
+        uint32_t k = 0u, M = eq;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            if (b < nb) {
+                const uint32_t bit = (c[b] >> l0) & 1u;
+                k |= bit << b;
+                M &= bit ? c[b] : ~c[b];
+            }
+        }
         eq &= ~M;
         const uint64_t thr = thr_of(k);
         if (thr == 0ull) continue;
@@ -353,7 +378,8 @@ struct WordOut {
 // SIR / SIS word update from counts of infected in-arcs (Appendix A.1 rules).
 template <int MODEL, int B>
 __device__ __forceinline__ WordOut update_sir_word(const StepArgs &A, uint32_t v, const WordCtx &x,
-                                                   uint32_t s0, uint32_t s1, const uint32_t (&c)[B]) {
+                                                   uint32_t s0, uint32_t s1, int32_t d,
+                                                   const uint32_t (&c)[B]) {
     const SetParams &p = A.sp[x.s];
     const uint32_t S = x.vm & ~s0 & ~s1;
     const uint32_t cand = S & any_count<B>(c);
@@ -366,8 +392,10 @@ __device__ __forceinline__ WordOut update_sir_word(const StepArgs &A, uint32_t v
         uint32_t below = 0u;
         if (rem) {
             const uint64_t *surv = p.surv;
-            below = grouped_u_less<B>(c, rem, [surv](uint32_t k) { return __ldg(surv + k); }, v,
-                                      A.t, x.g, TAG_INFECT, x.k0, x.k1);
+            // counts of rem lanes are at most d and below K_sat (the surv table covers both)
+            const uint32_t kcap = (uint32_t)min(d, ksat - 1);
+            below = grouped_u_less<B>(c, rem, [surv](uint32_t k) { return __ldg(surv + k); }, kcap,
+                                      v, A.t, x.g, TAG_INFECT, x.k0, x.k1);
         }
         infect = sat | (rem & ~below);   // infected iff u >= surv[k]
     }
@@ -393,7 +421,7 @@ __device__ __forceinline__ WordOut update_lt_word(const StepArgs &A, uint32_t v,
             const uint64_t dd = (uint64_t)d;
             act = grouped_u_less<B>(c, rem,
                                     [dd](uint32_t k) { return ((uint64_t)k << 32) / dd + 1ull; },
-                                    v, 0u, x.g, TAG_LT_THRESH, x.k0, x.k1);
+                                    (uint32_t)(d - 1), v, 0u, x.g, TAG_LT_THRESH, x.k0, x.k1);
         }
         act |= sat;
     }
@@ -502,9 +530,9 @@ __device__ __forceinline__ void list_append(const StepArgs &A, bool build, bool 
 // Launch shape of the row kernels of one step (host side).
 struct StepLaunch {
     int V, TEAM;           // words per thread, threads per slice team
-    int grid_small, grid_mid, grid_hub, grid_fin, grid_zero;
+    int grid_small, grid_mid, grid_hub, grid_fin, grid_zero, grid_small4, grid_tiny;
     size_t smem_lanes;     // dynamic shared memory for per-lane counters (0 = off)
-    bool have_small, have_mid, have_hub, have_zero;
+    bool have_small, have_mid, have_hub, have_zero, have_small4, have_tiny;
     struct Prof *prof;     // host-side event recorder, or null
 };
 
@@ -548,9 +576,11 @@ int run_sets(fsgp_graph *g, int model, int ic_mode, const SetSpec *sets, int n_s
 // Defined in rows.cuh, instantiated once per model (model_*.cu).
 template <int MODEL>
 int launch_rows(const StepArgs &A, const StepLaunch &L, cudaStream_t s);
+struct RowOccupancy {
+    int small, small4, tiny, zero, mid, hub;   // resident CTAs per SM of each row kernel
+};
 template <int MODEL>
-int occupancy_rows(int V, int TEAM, size_t smem, int *bps_rows, int *bps_mid, int *bps_hub,
-                   int *bps_zero);
+int occupancy_rows(int V, int TEAM, size_t smem, RowOccupancy *o);
 template <int MODEL>
 int launch_split_rows(const StepArgs &A, int V, int TEAM, int grid_chunks, int grid_fin,
                       cudaStream_t s);
