@@ -112,8 +112,7 @@ constexpr int min_ctas() { return V == 4 ? 2 : (V == 2 ? (WIDE ? 3 : 4) : 4); }
 // BT: counter bits of a team kernel, sized to its rows' in-degree bound (fewer planes =
 // fewer registers and cheaper counting and grouping).
 // which: 0 = small rows with 16..small_max in-arcs (and every small row of a frontier
-// step), 1 = mid rows, 2 = rows with 1..3 in-arcs, 3 = rows with 4..15 in-arcs (2 and 3:
-// dense steps only).
+// step), 1 = mid rows, 3 = rows with 4..15 in-arcs (dense steps only).
 template <int MODEL, int V, int TEAM, bool WARP_ROW, int BT = kSmallBits>
 __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepArgs A, int which) {
     extern __shared__ int32_t s_lane[];
@@ -132,8 +131,8 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
         rows = which ? A.cand_mid : A.cand_small;
         nrows = (int64_t)((volatile const uint32_t *)C->cand_n)[which];
     } else {
-        rows = which == 0 ? A.rows_small : which == 1 ? A.rows_mid : which == 2 ? A.rows_tiny : A.rows_small4;
-        nrows = which == 0 ? A.n_small : which == 1 ? A.n_mid : which == 2 ? A.n_tiny : A.n_small4;
+        rows = which == 0 ? A.rows_small : which == 1 ? A.rows_mid : A.rows_small4;
+        nrows = which == 0 ? A.n_small : which == 1 ? A.n_mid : A.n_small4;
     }
     if (nrows == 0) return;
     const int nl = A.Wn * 32;
@@ -508,22 +507,31 @@ __global__ void __launch_bounds__(kBlock) k_hub_finalize(StepArgs A) {
     if (lanes_on) flush_lanes(A, s_lane, nl);
 }
 
-// Rows without in-arcs, dense steps only (on frontier steps such rows come through the
-// candidate lists of k_rows): nothing to gather, so a lane changes only by recovery
-// (SIR/SIS) or by the newly-active plane clearing (IC/LT) -- the update of k_rows with
-// all counts zero.  One team per (row, slice) item; the next item's row id and state
-// words are loaded one item ahead, which the missing counters leave registers for.
-template <int MODEL, int V, int TEAM>
-__global__ void __launch_bounds__(kBlock) k_static_rows(StepArgs A) {
+// Rows with at most 3 in-arcs (including none), dense steps only (on frontier steps
+// such rows come through the candidate lists of k_rows).  Most rows of a power-law graph
+// are of this kind and carry little gather work, so the cost is the chain of dependent
+// loads per row: one THREAD per item (a slice of SWL <= 8 words of one row) keeps four
+// to eight times as many rows in flight per SM as a team per row.  The thread loads its
+// own words and the (at most three) sources' words at once, stages them in shared memory,
+// and then decides its words one at a time through a single, non-unrolled copy of the
+// per-word update (counts of at most 3 need 2-bit counters).
+constexpr int kLaneMaxDeg = 3;
+template <int SWL>
+struct LaneStage {
+    uint32_t v[5][SWL][kBlock];   // own planes 0/1, then the sources' words (x0, x1, x2)
+};
+
+template <int MODEL, int SWL>
+__global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
     extern __shared__ int32_t s_lane[];
     __shared__ unsigned long long s_pc[2 * kMaxSets];
-    constexpr int TPW = 32 / TEAM;
-    constexpr int SW = TEAM * V;
+    __shared__ LaneStage<SWL> st;
     constexpr int P = ModelTraits<MODEL>::planes;
     const Ctl *C = A.ctl;
     if (*(volatile const int32_t *)&C->stop) return;
     if (*(volatile const int32_t *)&C->sparse) return;
-    const int64_t nitems = (int64_t)A.n_zero * A.nslices;
+    const int nsl = A.Wn / SWL;
+    const int64_t nitems = (int64_t)A.n_lane * nsl;
     if (nitems == 0) return;
     const int nl = A.Wn * 32;
     const bool lanes_on = A.lane_cnt != nullptr;
@@ -531,109 +539,158 @@ __global__ void __launch_bounds__(kBlock) k_static_rows(StepArgs A) {
     if (lanes_on)
         for (int i = threadIdx.x; i < 2 * nl; i += blockDim.x) s_lane[i] = 0;
     set_acc_zero(s_pc, A.S);
-    const int lane = threadIdx.x & 31;
-    const int team = lane / TEAM;
-    const int tl = lane % TEAM;
-    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int list_slot = A.k & 1;
-    const int64_t stride = nwarps * TPW;
+    const int tid = threadIdx.x;
+    const uint32_t *src_plane = A.cur + (size_t)ModelTraits<MODEL>::src_plane * A.plane_words;
     Accum acc;
-    int ctx_slice = -1;
-    WordCtx x[V];
-    int32_t d0[V], d1[V];
+    int cur_s = -1;           // set of the plane-count deltas not yet flushed
+    int32_t dd0 = 0, dd1 = 0;
+    for (int64_t item = (int64_t)blockIdx.x * blockDim.x + tid; item - tid < nitems;
+         item += (int64_t)gridDim.x * blockDim.x) {
+        const bool has = item < nitems;
+        int32_t v = 0, beg = 0, d = 0;
+        int w0 = 0;
+        if (has) {
+            const int64_t r = item / nsl;
+            w0 = (int)(item - r * nsl) * SWL;
+            v = __ldg(A.rows_lane + r);
+            beg = __ldg(A.row_ptr + v);
+            d = __ldg(A.row_ptr + v + 1) - beg;
+            const size_t off = (size_t)v * A.Wn + w0;
+            int32_t u[kLaneMaxDeg];
 #pragma unroll
-    for (int i = 0; i < V; ++i) d0[i] = d1[i] = 0;
-    // item -> (row id, slice, own words), loaded one item ahead
-    auto fetch = [&](int64_t it, int32_t &v, int &slice, uint32_t (&a)[V], uint32_t (&b)[V]) {
-        v = 0;
-        slice = 0;
+            for (int j = 0; j < kLaneMaxDeg; ++j) u[j] = j < d ? __ldg(A.col + beg + j) : -1;
+            // own words and sources' words, 4 (or fewer) words per load
 #pragma unroll
-        for (int i = 0; i < V; ++i) a[i] = b[i] = 0u;
-        if (it < nitems) {
-            const int64_t r = it / A.nslices;
-            slice = (int)(it - r * A.nslices);
-            v = __ldg(A.rows_zero + r);
-            const size_t off = (size_t)v * A.Wn + slice * SW + tl * V;
-            const Vec<V> va = ldg_vec<V>(A.cur + off);
+            for (int q = 0; q < SWL; q += (SWL < 4 ? SWL : 4)) {
+                constexpr int VL = SWL < 4 ? SWL : 4;
+                const Vec<VL> a = ldg_vec<VL>(A.cur + off + q);
+                Vec<VL> bb{};
+                if (P == 2) bb = ldg_vec<VL>(A.cur + A.plane_words + off + q);
 #pragma unroll
-            for (int i = 0; i < V; ++i) a[i] = va.w[i];
-            if (P == 2) {
-                const Vec<V> vb = ldg_vec<V>(A.cur + A.plane_words + off);
+                for (int i = 0; i < VL; ++i) {
+                    st.v[0][q + i][tid] = a.w[i];
+                    st.v[1][q + i][tid] = P == 2 ? bb.w[i] : 0u;
+                }
 #pragma unroll
-                for (int i = 0; i < V; ++i) b[i] = vb.w[i];
+                for (int j = 0; j < kLaneMaxDeg; ++j) {
+                    Vec<VL> x{};
+                    if (u[j] >= 0) x = ldg_vec<VL>(src_plane + (size_t)u[j] * A.Wn + w0 + q);
+#pragma unroll
+                    for (int i = 0; i < VL; ++i) st.v[2 + j][q + i][tid] = x.w[i];
+                }
             }
-        }
-    };
-    int64_t item = gwarp * TPW + team;
-    int32_t v_nx;
-    int slice_nx;
-    uint32_t a_nx[V], b_nx[V];
-    fetch(item, v_nx, slice_nx, a_nx, b_nx);
-    for (int64_t base = gwarp * TPW; base < nitems; base += stride, item += stride) {
-        const bool has_row = item < nitems;
-        const int32_t v = v_nx;
-        const int slice = slice_nx;
-        uint32_t s0[V], s1[V];
-#pragma unroll
-        for (int i = 0; i < V; ++i) {
-            s0[i] = a_nx[i];
-            s1[i] = b_nx[i];
-        }
-        fetch(item + stride, v_nx, slice_nx, a_nx, b_nx);
-        const int w0 = slice * SW + tl * V;
-        if (has_row && slice != ctx_slice) {
-#pragma unroll
-            for (int i = 0; i < V; ++i) {
-                if (ctx_slice >= 0) set_acc_add(s_pc, x[i].s, d0[i], d1[i]);
-                d0[i] = d1[i] = 0;
-                x[i] = word_ctx(A, w0 + i);
-            }
-            ctx_slice = slice;
         }
         uint32_t fl = 0u;
-        if (has_row) {
-            uint32_t n0[V], n1[V];
+        if (has) {
+#pragma unroll 1
+            for (int i = 0; i < SWL; ++i) {
+                const WordCtx x = word_ctx(A, w0 + i);
+                const uint32_t s0 = st.v[0][i][tid], s1 = st.v[1][i][tid];
+                const uint32_t x0 = st.v[2][i][tid], x1 = st.v[3][i][tid], x2 = st.v[4][i][tid];
+                WordOut o;
+                if constexpr (MODEL == FSGP_IC) {
+                    const uint32_t need = x.vm & ~s0;
+                    const uint64_t thr = ic_threshold(A, x.s, d);
+                    uint32_t newly = 0u;
+                    const uint32_t xs[kLaneMaxDeg] = {x0, x1, x2};
 #pragma unroll
-            for (int i = 0; i < V; ++i) {
-                if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SIS) {
-                    const SetParams &p = A.sp[x[i].s];
-                    const uint32_t rec = lanes_u_less(s0[i] & x[i].vm, __ldg(&p.g_rec), (uint32_t)v, A.t,
-                                                      x[i].g, TAG_RECOVER, x[i].k0, x[i].k1);
-                    n0[i] = s0[i] & ~rec;
-                    n1[i] = MODEL == FSGP_SIR ? (s1[i] | rec) : 0u;
+                    for (int j = 0; j < kLaneMaxDeg; ++j) {
+                        const uint32_t m = xs[j] & need & ~newly;
+                        if (m) newly |= lanes_u_less(m, thr, (uint32_t)(beg + j), A.t, x.g, TAG_IC_EDGE, x.k0, x.k1);
+                    }
+                    o.n0 = s0 | newly;
+                    o.n1 = newly;
                 } else {
-                    n0[i] = s0[i];
-                    n1[i] = 0u;
+                    // counts of set source lanes (at most 3): two bit-planes
+                    uint32_t c[2];
+                    c[0] = x0 ^ x1 ^ x2;
+                    c[1] = (x0 & x1) | (x2 & (x0 ^ x1));
+                    if constexpr (MODEL == FSGP_LT) {
+                        const uint32_t need = x.vm & ~s0;
+                        c[0] &= need;
+                        c[1] &= need;
+                        o = update_lt_word<2>(A, (uint32_t)v, x, s0, d, c);
+                    } else {
+                        const uint32_t need = x.vm & ~s0 & ~s1;
+                        c[0] &= need;
+                        c[1] &= need;
+                        o = update_sir_word<MODEL, 2>(A, (uint32_t)v, x, s0, s1, d, c);
+                    }
                 }
-                d0[i] += __popc(n0[i]) - __popc(s0[i]);
-                d1[i] += __popc(n1[i]) - __popc(s1[i]);
+                st.v[0][i][tid] = o.n0;
+                st.v[1][i][tid] = o.n1;
+                if (x.s != cur_s) {
+                    if (cur_s >= 0) set_acc_add(s_pc, cur_s, dd0, dd1);
+                    cur_s = x.s;
+                    dd0 = dd1 = 0;
+                }
+                dd0 += __popc(o.n0) - __popc(s0);
+                dd1 += __popc(o.n1) - __popc(s1);
                 if (lanes_on) {
-                    lane_deltas(s_lane, w0 + i, s0[i], n0[i]);
-                    if (P == 2) lane_deltas(s_lane + nl, w0 + i, s1[i], n1[i]);
+                    lane_deltas(s_lane, w0 + i, s0, o.n0);
+                    if (P == 2) lane_deltas(s_lane + nl, w0 + i, s1, o.n1);
                 }
-                if (n0[i] != s0[i] || n1[i] != s1[i]) fl |= 2u;
-                if ((MODEL == FSGP_SIR || MODEL == FSGP_SIS) ? (n0[i] != 0u) : (n1[i] != 0u)) fl |= 1u;
+                if (o.n0 != s0 || o.n1 != s1) fl |= 2u;
+                if ((MODEL == FSGP_SIR || MODEL == FSGP_SIS) ? (o.n0 != 0u) : (o.n1 != 0u)) fl |= 1u;
             }
             const size_t off = (size_t)v * A.Wn + w0;
-            st_vec<V>(A.nxt + off, n0);
-            if (P == 2) st_vec<V>(A.nxt + A.plane_words + off, n1);
-        }
 #pragma unroll
-        for (int o = 1; o < TEAM; o <<= 1) fl |= __shfl_xor_sync(0xffffffffu, fl, o);
-        const bool leader = has_row && tl == 0;
-        const bool want = leader && fl != 0u;
+            for (int q = 0; q < SWL; q += (SWL < 4 ? SWL : 4)) {
+                constexpr int VL = SWL < 4 ? SWL : 4;
+                uint32_t n0[VL], n1[VL];
+#pragma unroll
+                for (int i = 0; i < VL; ++i) {
+                    n0[i] = st.v[0][q + i][tid];
+                    n1[i] = st.v[1][q + i][tid];
+                }
+                st_vec<VL>(A.nxt + off + q, n0);
+                if (P == 2) st_vec<VL>(A.nxt + A.plane_words + off + q, n1);
+            }
+        }
+        const bool want = has && fl != 0u;
         if (want && (fl & 1u)) acc.push_deg += (unsigned long long)(__ldg(A.out_ptr + v + 1) - __ldg(A.out_ptr + v));
-        if (A.prof_bytes && leader) acc.bytes += row_bytes(SW, P, false, 0);
+        if (A.prof_bytes && has) acc.bytes += row_bytes(SWL, P, d > 0, d);
         list_append(A, build, want, (int32_t)((uint32_t)v | ((fl & 1u) ? kPushBit : 0u)), list_slot);
     }
-    if (ctx_slice >= 0) {
-#pragma unroll
-        for (int i = 0; i < V; ++i) set_acc_add(s_pc, x[i].s, d0[i], d1[i]);
-    }
+    if (cur_s >= 0) set_acc_add(s_pc, cur_s, dd0, dd1);
     flush_accum(A, acc, list_slot, PK_SMALL);
     set_acc_flush(A, s_pc);
     if (lanes_on) flush_lanes(A, s_lane, nl);
+}
+
+template <int MODEL>
+int launch_rows_lane(const StepArgs &A, int swl, int grid, size_t smem, cudaStream_t s) {
+    switch (swl) {
+        case 1: k_rows_lane<MODEL, 1><<<grid, kBlock, smem, s>>>(A); break;
+        case 2: k_rows_lane<MODEL, 2><<<grid, kBlock, smem, s>>>(A); break;
+        case 4: k_rows_lane<MODEL, 4><<<grid, kBlock, smem, s>>>(A); break;
+        case 8: k_rows_lane<MODEL, 8><<<grid, kBlock, smem, s>>>(A); break;
+        default: return fail(FSGP_EINVAL, "lane kernel slice width");
+    }
+    return FSGP_OK;
+}
+
+template <int MODEL, int SWL>
+int occupancy_lane_w(size_t smem) {
+    // the staging area is static; per-lane counters (dynamic) may push the total past the
+    // default 48 KB window (set before any launch or capture)
+    cudaFuncSetAttribute(k_rows_lane<MODEL, SWL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int z = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&z, k_rows_lane<MODEL, SWL>, kBlock, smem);
+    return z;
+}
+
+template <int MODEL>
+int occupancy_lane(int swl, size_t smem) {
+    int z = 1;
+    switch (swl) {
+        case 1: z = occupancy_lane_w<MODEL, 1>(smem); break;
+        case 2: z = occupancy_lane_w<MODEL, 2>(smem); break;
+        case 4: z = occupancy_lane_w<MODEL, 4>(smem); break;
+        default: z = occupancy_lane_w<MODEL, 8>(smem); break;
+    }
+    return z < 1 ? 1 : z;
 }
 
 // ------------------------------------------------------------------------- launch
@@ -663,34 +720,26 @@ int launch_rows_vt(const StepArgs &A, const StepLaunch &L, cudaStream_t s) {
         k_rows<MODEL, V, TEAM, false, 4><<<L.grid_small4, kBlock, L.smem_lanes, s>>>(A, 3);
         if (pr) pr->stop(s);
     }
-    if (L.have_tiny) {
+    if (L.have_lane) {
         if (pr) pr->start(PK_SMALL, s);
-        k_rows<MODEL, V, TEAM, false, 2><<<L.grid_tiny, kBlock, L.smem_lanes, s>>>(A, 2);
+        const int rc = launch_rows_lane<MODEL>(A, L.swl, L.grid_lane, L.smem_lanes, s);
         if (pr) pr->stop(s);
-    }
-    if (L.have_zero) {
-        if (pr) pr->start(PK_SMALL, s);
-        k_static_rows<MODEL, V, TEAM><<<L.grid_zero, kBlock, L.smem_lanes, s>>>(A);
-        if (pr) pr->stop(s);
+        if (rc) return rc;
     }
     return FSGP_OK;
 }
 
 template <int MODEL, int V, int TEAM>
 void occupancy_vt(size_t smem, RowOccupancy *o) {
-    int a = 1, m = 1, b = 1, z = 1, s4 = 1, s2 = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&z, k_static_rows<MODEL, V, TEAM>, kBlock, smem);
+    int a = 1, m = 1, b = 1, s4 = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s4, k_rows<MODEL, V, TEAM, false, 4>, kBlock, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s2, k_rows<MODEL, V, TEAM, false, 2>, kBlock, smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_rows<MODEL, V, TEAM, false>, kBlock, smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k_rows<MODEL, V, TEAM, true>, kBlock, smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_hub_chunks<MODEL, V, TEAM>, kBlock, 0);
     o->small = a < 1 ? 1 : a;
     o->mid = m < 1 ? 1 : m;
     o->hub = b < 1 ? 1 : b;
-    o->zero = z < 1 ? 1 : z;
     o->small4 = s4 < 1 ? 1 : s4;
-    o->tiny = s2 < 1 ? 1 : s2;
 }
 
 #define FSGP_VT_SWITCH(MACRO)                          \
@@ -748,6 +797,7 @@ int occupancy_rows(int V, int TEAM, size_t smem, RowOccupancy *o) {
 #define FSGP_O(v_, t_) occupancy_vt<MODEL, v_, t_>(smem, o)
     FSGP_VT_SWITCH(FSGP_O)
 #undef FSGP_O
+    o->lane = occupancy_lane<MODEL>(o->swl, smem);
     return FSGP_OK;
 }
 

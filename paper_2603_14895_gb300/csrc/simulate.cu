@@ -456,12 +456,10 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     const int32_t n_mid = start_small - start_mid;
     // small rows by in-degree class; rows_sorted holds the buckets in descending order
     // (bucket b: 2^(b-1) <= d < 2^b, bucket 0: d = 0), so each class is one range
-    const int32_t start_zero = g->cls.bucket_start[0];
-    const int32_t start_tiny = bs >= 2 ? g->cls.bucket_start[2] : start_small;     // d 1..3
+    const int32_t start_lane = std::max(bs >= 2 ? g->cls.bucket_start[2] : start_small, start_small);  // d 0..3
     const int32_t start_small4 = bs >= 4 ? g->cls.bucket_start[4] : start_small;   // d 4..15
-    const int32_t n_zero = n - start_zero;
-    const int32_t n_tiny = start_zero - std::max(start_tiny, start_small);
-    const int32_t n_small4 = std::max(start_tiny, start_small) - std::max(start_small4, start_small);
+    const int32_t n_lane = n - start_lane;
+    const int32_t n_small4 = start_lane - std::max(start_small4, start_small);
     const int32_t n_small = std::max(start_small4, start_small) - start_small;        // d 16..small_max
     const int32_t n_small_all = n - start_small;
 
@@ -504,7 +502,8 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     sz[O_STATE] = 2 * state_words * sizeof(uint32_t);
     sz[O_PC] = T1 * S * 2 * sizeof(unsigned long long);
     sz[O_CTL] = sizeof(Ctl);
-    sz[O_LIST0] = sz[O_LIST1] = (size_t)n * nslices * sizeof(int32_t);
+    // a row is listed once per work item: slices of the team kernels or of the lane kernel
+    sz[O_LIST0] = sz[O_LIST1] = (size_t)n * std::max(nslices, Wn / std::min(8, pd)) * sizeof(int32_t);
     sz[O_CSMALL] = sz[O_CMID] = (size_t)n * sizeof(int32_t);
     sz[O_BITMAP] = ((size_t)n + 31) / 32 * sizeof(uint32_t);
     sz[O_LANES] = want_lanes ? 2 * (size_t)Wn * 32 * sizeof(int32_t) : 0;
@@ -565,6 +564,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     const size_t smem_lanes = want_lanes ? 2 * (size_t)Wn * 32 * sizeof(int32_t) : 0;
     if (smem_lanes > 32 * 1024) return fail(FSGP_EINVAL, "per-lane counters exceed shared memory");
     RowOccupancy occ{};
+    occ.swl = std::min(8, pd);   // words per thread of the one-thread-per-row kernel
     rc = occupancy_model(model, V, TEAM, smem_lanes, &occ);
     if (rc) return rc;
     Prof prof;
@@ -577,13 +577,13 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     // the 16..small_max kernel also takes every small row of a frontier step
     L.have_small = n_small_all > 0;
     L.have_small4 = n_small4 > 0;
-    L.have_tiny = n_tiny > 0;
-    L.have_zero = n_zero > 0;
+    L.have_lane = n_lane > 0;
+    L.swl = occ.swl;
     L.have_mid = n_mid > 0;
     L.have_hub = n_hubs > 0;
     L.prof = profiling ? &prof : nullptr;
     const int64_t items_small = (int64_t)n_small_all * nslices, items_mid = (int64_t)n_mid * nslices;
-    const int64_t items_zero = (int64_t)n_zero * nslices;
+    const int64_t items_lane = (int64_t)n_lane * (Wn / occ.swl);
     const int per_block_small = (kBlock / 32) * (32 / TEAM);
     auto grid_for_items = [&](int per_sm, int64_t items) {
         return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * per_sm,
@@ -591,13 +591,14 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     };
     L.grid_small = grid_for_items(occ.small, items_small);
     L.grid_small4 = grid_for_items(occ.small4, (int64_t)n_small4 * nslices);
-    L.grid_tiny = grid_for_items(occ.tiny, (int64_t)n_tiny * nslices);
+    L.grid_lane = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * occ.lane,
+                                                              (items_lane + kBlock - 1) / kBlock));
     L.grid_mid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * occ.mid,
                                                              (items_mid + (kBlock / 32) - 1) / (kBlock / 32)));
     L.grid_hub = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * occ.hub,
                                                              g->hub.n_chunks * nslices));
     L.grid_fin = (int)std::max<int64_t>(1, ((int64_t)n_hubs + (kBlock / 32) - 1) / (kBlock / 32));
-    L.grid_zero = grid_for_items(occ.zero, items_zero);
+
     const int grid_mark = g->sm_count * 8;
     const int grid_scan = grid_cap((int64_t)n, kBlock, g->sm_count, 8);
 
@@ -622,11 +623,9 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     A.lane_cnt = want_lanes ? (int32_t *)(ws + off[O_LANES]) : nullptr;
     A.rows_small = g->rows_sorted + start_small;
     A.rows_small4 = g->rows_sorted + std::max(start_small4, start_small);
-    A.rows_tiny = g->rows_sorted + std::max(start_tiny, start_small);
-    A.rows_zero = g->rows_sorted + start_zero;
-    A.n_zero = n_zero;
+    A.rows_lane = g->rows_sorted + start_lane;
+    A.n_lane = n_lane;
     A.n_small4 = n_small4;
-    A.n_tiny = n_tiny;
     A.rows_mid = g->rows_sorted + start_mid;
     A.n_small = n_small;
     A.n_mid = n_mid;
@@ -723,8 +722,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
         rc = launch_rows_model(model, A, L, s);
         if (rc) return rc;
         launches += 1 + (allow_sparse ? 1 : 0) + (L.have_hub ? 2 : 0) + (L.have_mid ? 1 : 0) +
-                    (L.have_small ? 1 : 0) + (L.have_zero ? 1 : 0) + (L.have_small4 ? 1 : 0) +
-                    (L.have_tiny ? 1 : 0);
+                    (L.have_small ? 1 : 0) + (L.have_small4 ? 1 : 0) + (L.have_lane ? 1 : 0);
     }
     FSGP_CUDA(cudaGetLastError());
     if (profiling) prof.start(PK_RESULTS, s);

@@ -85,13 +85,12 @@ struct StepArgs {
     unsigned long long *pc;        // [S][2] plane popcounts of this step (running totals)
     int32_t *lane_cnt;             // [2][Wn*32] running per-lane plane counts, or null
     // row lists
-    // dense steps: small rows by in-degree class (16.., 4..15, 1..3, 0), mid rows
+    // dense steps: small rows by in-degree class (16.., 4..15, 0..3), mid rows
     const int32_t *__restrict__ rows_small;
     const int32_t *__restrict__ rows_small4;
-    const int32_t *__restrict__ rows_tiny;
-    const int32_t *__restrict__ rows_zero;
+    const int32_t *__restrict__ rows_lane;
     const int32_t *__restrict__ rows_mid;
-    int32_t n_small, n_small4, n_tiny, n_zero, n_mid;
+    int32_t n_small, n_small4, n_lane, n_mid;
     int32_t *cand_small;
     int32_t *cand_mid;
     uint32_t *bitmap;
@@ -530,9 +529,10 @@ __device__ __forceinline__ void list_append(const StepArgs &A, bool build, bool 
 // Launch shape of the row kernels of one step (host side).
 struct StepLaunch {
     int V, TEAM;           // words per thread, threads per slice team
-    int grid_small, grid_mid, grid_hub, grid_fin, grid_zero, grid_small4, grid_tiny;
+    int grid_small, grid_mid, grid_hub, grid_fin, grid_small4, grid_lane;
+    int swl;               // words per thread of the one-thread-per-row kernel
     size_t smem_lanes;     // dynamic shared memory for per-lane counters (0 = off)
-    bool have_small, have_mid, have_hub, have_zero, have_small4, have_tiny;
+    bool have_small, have_mid, have_hub, have_small4, have_lane;
     struct Prof *prof;     // host-side event recorder, or null
 };
 
@@ -577,7 +577,8 @@ int run_sets(fsgp_graph *g, int model, int ic_mode, const SetSpec *sets, int n_s
 template <int MODEL>
 int launch_rows(const StepArgs &A, const StepLaunch &L, cudaStream_t s);
 struct RowOccupancy {
-    int small, small4, tiny, zero, mid, hub;   // resident CTAs per SM of each row kernel
+    int small, small4, lane, mid, hub;   // resident CTAs per SM of each row kernel
+    int swl;                             // in: slice width of the lane kernel
 };
 template <int MODEL>
 int occupancy_rows(int V, int TEAM, size_t smem, RowOccupancy *o);
