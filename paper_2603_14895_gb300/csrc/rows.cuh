@@ -102,6 +102,16 @@ __device__ __forceinline__ void gather_arcs(const StepArgs &A, int64_t e_begin, 
     }
 }
 
+// Counter plane b of word i of a thread's V words, by selects (i is not a compile-time
+// constant where this is used; indexing the array with it would move it to local memory).
+template <int V, int B>
+__device__ __forceinline__ uint32_t pick(const uint32_t (&c)[V][B], int i, int b) {
+    uint32_t r = c[0][b];
+#pragma unroll
+    for (int q = 1; q < V; ++q) r = i == q ? c[q][b] : r;
+    return r;
+}
+
 // Resident CTAs per SM the register allocation is bounded for: wider thread words hold
 // more counters, narrower ones run more warps to keep more loads in flight.
 template <int V, bool WIDE>
@@ -234,8 +244,60 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
                 }
             }
         }
-        const bool writer = has_row && (!WARP_ROW || team == 0);
         uint32_t fl = 0u;
+        bool writer;
+        constexpr bool SPLIT = WARP_ROW && TPW >= V;   // enough teams to give each word one
+        if constexpr (SPLIT) {
+            // every team holds the merged counts of the same words: team i < V decides the
+            // i-th word of each thread's V words, so the decisions of a row run V-wide
+            // instead of V-deep
+            writer = has_row && team < V;
+            if (writer) {
+                const int i = team;
+                uint32_t cw[B];
+#pragma unroll
+                for (int b = 0; b < B; ++b) cw[b] = pick<V, B>(c, i, b);
+                WordCtx xw = x[0];
+                uint32_t nw = newly[0];
+#pragma unroll
+                for (int q = 1; q < V; ++q) {
+                    if (i == q) {
+                        xw = x[q];
+                        nw = newly[q];
+                    }
+                }
+                const uint32_t s0 = __ldg(A.cur + off + i);
+                const uint32_t s1 = P == 2 ? __ldg(A.cur + A.plane_words + off + i) : 0u;
+                WordOut o;
+                if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SIS) {
+                    o = update_sir_word<MODEL, B>(A, (uint32_t)v, xw, s0, s1, end - beg, cw);
+                } else if constexpr (MODEL == FSGP_IC) {
+                    o.n0 = s0 | nw;
+                    o.n1 = nw;
+                } else {
+                    o = update_lt_word<B>(A, (uint32_t)v, xw, s0, end - beg, cw);
+                }
+                A.nxt[off + i] = o.n0;
+                if (P == 2) A.nxt[A.plane_words + off + i] = o.n1;
+#pragma unroll
+                for (int q = 0; q < V; ++q) {
+                    if (i == q) {
+                        d0[q] += __popc(o.n0) - __popc(s0);
+                        d1[q] += __popc(o.n1) - __popc(s1);
+                    }
+                }
+                if (lanes_on) {
+                    lane_deltas(s_lane, w0 + i, s0, o.n0);
+                    if (P == 2) lane_deltas(s_lane + nl, w0 + i, s1, o.n1);
+                }
+                if (o.n0 != s0 || o.n1 != s1) fl |= 2u;
+                if ((MODEL == FSGP_SIR || MODEL == FSGP_SIS) ? (o.n0 != 0u) : (o.n1 != 0u)) fl |= 1u;
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+            writer = has_row && team == 0;
+        } else {
+        writer = has_row && (!WARP_ROW || team == 0);
         if (writer) {
             // own state again (L1/L2-resident): not kept live across the gather
             uint32_t s0[V], s1[V];
@@ -277,6 +339,7 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
         }
 #pragma unroll
         for (int o = 1; o < TEAM; o <<= 1) fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+        }
         const bool leader = writer && tl == 0;
         const bool want = leader && fl != 0u;
         if (want && (fl & 1u)) acc.push_deg += (unsigned long long)(__ldg(A.out_ptr + v + 1) - __ldg(A.out_ptr + v));
