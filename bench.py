@@ -563,10 +563,11 @@ def main():
 
     # per-kernel roofline from the profiled timed region
     kinds = fsgp.PROFILE_KINDS
-    agg_ms = [sum(profiles[m].ms[i] for m in MODELS) for i in range(8)]
-    agg_b = [sum(profiles[m].alg_bytes[i] for m in MODELS) for i in range(8)]
-    agg_n = [sum(profiles[m].launches[i] for m in MODELS) for i in range(8)]
-    dom = max(range(8), key=lambda i: agg_ms[i])
+    NK = len(kinds)
+    agg_ms = [sum(profiles[m].ms[i] for m in MODELS) for i in range(NK)]
+    agg_b = [sum(profiles[m].alg_bytes[i] for m in MODELS) for i in range(NK)]
+    agg_n = [sum(profiles[m].launches[i] for m in MODELS) for i in range(NK)]
+    dom = max(range(NK), key=lambda i: agg_ms[i])
     peak, peak_kind = measured_peaks()
     achieved = (agg_b[dom] / agg_n[dom]) / (agg_ms[dom] / agg_n[dom] / 1e3) / 1e9 if agg_n[dom] else 0.0
     traffic = ncu_traffic(kinds[dom])
@@ -574,7 +575,7 @@ def main():
     per_kernel = {kinds[i]: {"launches": agg_n[i] // args.steps,
                              "ms_per_step": agg_ms[i] / args.steps,
                              "alg_GBps": (agg_b[i] / (agg_ms[i] / 1e3) / 1e9) if agg_ms[i] else 0.0}
-                  for i in range(8) if agg_n[i]}
+                  for i in range(NK) if agg_n[i]}
     wall = {}
     for m, nm in zip(MODELS, ("SIR", "SIS")):
         wall[nm] = sum(profiles[m].ms) / args.steps / 1e3

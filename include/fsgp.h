@@ -95,9 +95,11 @@ typedef struct {
  * the rows it processed: 8 B of row pointers, the node's own state words read and
  * written (planes x 4 B x words), and per gathered in-arc 4 B of column index plus one
  * 32-byte sector (or more, for R > 256) of the source's state words. */
-#define FSGP_PROF_KINDS 8
+#define FSGP_PROF_KINDS 10
 /* kinds: 0 init, 1 step control, 2 frontier marking, 3 hub chunks, 4 hub finalize,
- *        5 warp-per-row rows, 6 team-per-row rows, 7 results */
+ *        5 warp-per-row rows, 6 team-per-row rows (16..255 in-arcs, and every small row
+ *        of a frontier step), 7 results, 8 team-per-row rows (4..15 in-arcs),
+ *        9 thread-per-row rows (0..3 in-arcs) */
 typedef struct {
     int64_t launches[FSGP_PROF_KINDS];
     double ms[FSGP_PROF_KINDS];

@@ -128,6 +128,10 @@ struct fsgp_graph {
     int32_t *out_ptr = nullptr;     // [n+1] out-CSR
     int32_t *out_dst = nullptr;     // [nnz]
     int32_t *rows_sorted = nullptr; // [n] rows by degree bucket, high buckets first
+    int2 *row_meta = nullptr;       // [n] {row_ptr[v], row_ptr[v+1]} of rows_sorted[i]
+    int4 *lane_tab = nullptr;       // rows with at most 3 in-arcs (the tail of rows_sorted
+                                    // from bucket 2 on): {v, col0, col1, col2}, -1 = none
+    int32_t lane_start = 0;         // index in rows_sorted of lane_tab[0]
     fsgp::ClassInfo cls{};
     fsgp::HubTable hub{};
     fsgp::Workspace ws{};

@@ -247,6 +247,26 @@ int exclusive_scan_i32(const int32_t *in, int64_t n, int32_t *out, int64_t *tile
     return FSGP_OK;
 }
 
+// Row pointers of the rows in bucket order, so the row kernels read a row's arc range
+// from a coalesced array instead of a random pair of row_ptr entries.
+__global__ void k_row_meta(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ rows, int32_t n,
+                           int2 *meta) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = rows[i];
+        meta[i] = make_int2(row_ptr[v], row_ptr[v + 1]);
+    }
+}
+
+// Rows with at most 3 in-arcs: the row and its (up to 3) sources in one 16-byte entry.
+__global__ void k_lane_tab(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                           const int32_t *__restrict__ rows, int32_t count, int4 *tab) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = rows[i];
+        const int32_t b = row_ptr[v], d = row_ptr[v + 1] - b;
+        tab[i] = make_int4(v, d > 0 ? col[b] : -1, d > 1 ? col[b + 1] : -1, d > 2 ? col[b + 2] : -1);
+    }
+}
+
 static void release(fsgp_graph *g) {
     if (!g) return;
     cudaFree(g->row_ptr);
@@ -254,6 +274,8 @@ static void release(fsgp_graph *g) {
     cudaFree(g->out_ptr);
     cudaFree(g->out_dst);
     cudaFree(g->rows_sorted);
+    cudaFree(g->row_meta);
+    cudaFree(g->lane_tab);
     cudaFree(g->hub.d_chunk_base);
     cudaFree(g->ws.ptr);
     cudaFree(g->sgc.inv_din);
@@ -421,6 +443,20 @@ extern "C" int fsgp_graph_create(const int32_t *row_ptr, const int32_t *col_idx,
                 break;
             }
         }
+        // bucket-ordered row pointers and the table of rows with at most 3 in-arcs
+        g->lane_start = g->cls.bucket_start[2];
+        const int32_t n_lane = n - g->lane_start;
+        if ((e = cudaMalloc(&g->row_meta, sizeof(int2) * (size_t)n)) != cudaSuccess ||
+            (n_lane > 0 && (e = cudaMalloc(&g->lane_tab, sizeof(int4) * (size_t)n_lane)) != cudaSuccess)) {
+            rc = cuda_fail(e, "cudaMalloc (row tables)");
+            break;
+        }
+        g->device_bytes += sizeof(int2) * (size_t)n + sizeof(int4) * (size_t)n_lane;
+        k_row_meta<<<grid_for(n, 256, g->sm_count), 256, 0, s>>>(g->row_ptr, g->rows_sorted, n, g->row_meta);
+        if (n_lane > 0)
+            k_lane_tab<<<grid_for(n_lane, 256, g->sm_count), 256, 0, s>>>(g->row_ptr, g->col,
+                                                                          g->rows_sorted + g->lane_start,
+                                                                          n_lane, g->lane_tab);
         if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess) {
             rc = cuda_fail(e, "graph build kernels");
             break;

@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
     if (*(volatile const int32_t *)&C->stop) return;
     const bool sparse = *(volatile const int32_t *)&C->sparse != 0;
     const int32_t *rows;
+    const int2 *meta = nullptr;   // dense steps: the rows' arc ranges, aligned with rows
     int64_t nrows;
     if (sparse) {
         if (which >= 2) return;
@@ -142,6 +143,7 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
         nrows = (int64_t)((volatile const uint32_t *)C->cand_n)[which];
     } else {
         rows = which == 0 ? A.rows_small : which == 1 ? A.rows_mid : A.rows_small4;
+        meta = which == 0 ? A.meta_small : which == 1 ? A.meta_mid : A.meta_small4;
         nrows = which == 0 ? A.n_small : which == 1 ? A.n_mid : A.n_small4;
     }
     if (nrows == 0) return;
@@ -214,8 +216,14 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
         }
         int32_t beg = 0, end = 0;
         if (has_row) {
-            beg = __ldg(A.row_ptr + v);
-            end = __ldg(A.row_ptr + v + 1);
+            if (meta) {
+                const int2 m = __ldg(meta + ridx);
+                beg = m.x;
+                end = m.y;
+            } else {
+                beg = __ldg(A.row_ptr + v);
+                end = __ldg(A.row_ptr + v + 1);
+            }
         }
         if (any_need) {
             uint64_t ic_thr[V];
@@ -351,7 +359,7 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
 #pragma unroll
         for (int i = 0; i < V; ++i) set_acc_add(s_pc, x[i].s, d0[i], d1[i]);
     }
-    flush_accum(A, acc, list_slot, WARP_ROW ? PK_MID : PK_SMALL);
+    flush_accum(A, acc, list_slot, WARP_ROW ? PK_MID : (BT == 4 ? PK_SMALL4 : PK_SMALL));
     set_acc_flush(A, s_pc);
     if (lanes_on) flush_lanes(A, s_lane, nl);
 }
@@ -616,13 +624,12 @@ __global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
         if (has) {
             const int64_t r = item / nsl;
             w0 = (int)(item - r * nsl) * SWL;
-            v = __ldg(A.rows_lane + r);
-            beg = __ldg(A.row_ptr + v);
-            d = __ldg(A.row_ptr + v + 1) - beg;
+            const int4 e = __ldg(A.lane_tab + r);   // the row and its sources in one entry
+            v = e.x;
+            const int32_t u[kLaneMaxDeg] = {e.y, e.z, e.w};
+            d = (e.y >= 0) + (e.z >= 0) + (e.w >= 0);
+            if (MODEL == FSGP_IC) beg = __ldg(&A.meta_lane[r].x);   // arc positions key the draws
             const size_t off = (size_t)v * A.Wn + w0;
-            int32_t u[kLaneMaxDeg];
-#pragma unroll
-            for (int j = 0; j < kLaneMaxDeg; ++j) u[j] = j < d ? __ldg(A.col + beg + j) : -1;
             // own words and sources' words, 4 (or fewer) words per load
 #pragma unroll
             for (int q = 0; q < SWL; q += (SWL < 4 ? SWL : 4)) {
@@ -717,7 +724,7 @@ __global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
         list_append(A, build, want, (int32_t)((uint32_t)v | ((fl & 1u) ? kPushBit : 0u)), list_slot);
     }
     if (cur_s >= 0) set_acc_add(s_pc, cur_s, dd0, dd1);
-    flush_accum(A, acc, list_slot, PK_SMALL);
+    flush_accum(A, acc, list_slot, PK_LANE);
     set_acc_flush(A, s_pc);
     if (lanes_on) flush_lanes(A, s_lane, nl);
 }
@@ -779,12 +786,12 @@ int launch_rows_vt(const StepArgs &A, const StepLaunch &L, cudaStream_t s) {
         if (pr) pr->stop(s);
     }
     if (L.have_small4) {
-        if (pr) pr->start(PK_SMALL, s);
+        if (pr) pr->start(PK_SMALL4, s);
         k_rows<MODEL, V, TEAM, false, 4><<<L.grid_small4, kBlock, L.smem_lanes, s>>>(A, 3);
         if (pr) pr->stop(s);
     }
     if (L.have_lane) {
-        if (pr) pr->start(PK_SMALL, s);
+        if (pr) pr->start(PK_LANE, s);
         const int rc = launch_rows_lane<MODEL>(A, L.swl, L.grid_lane, L.smem_lanes, s);
         if (pr) pr->stop(s);
         if (rc) return rc;

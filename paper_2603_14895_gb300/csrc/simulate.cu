@@ -624,6 +624,11 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     A.rows_small = g->rows_sorted + start_small;
     A.rows_small4 = g->rows_sorted + std::max(start_small4, start_small);
     A.rows_lane = g->rows_sorted + start_lane;
+    A.meta_small = g->row_meta + start_small;
+    A.meta_small4 = g->row_meta + std::max(start_small4, start_small);
+    A.meta_mid = g->row_meta + start_mid;
+    A.meta_lane = g->row_meta + start_lane;
+    A.lane_tab = g->lane_tab ? g->lane_tab + (start_lane - g->lane_start) : nullptr;
     A.n_lane = n_lane;
     A.n_small4 = n_small4;
     A.rows_mid = g->rows_sorted + start_mid;

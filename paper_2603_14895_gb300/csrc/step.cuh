@@ -91,6 +91,12 @@ struct StepArgs {
     const int32_t *__restrict__ rows_lane;
     const int32_t *__restrict__ rows_mid;
     int32_t n_small, n_small4, n_lane, n_mid;
+    // {row_ptr[v], row_ptr[v+1]} aligned with rows_small / rows_small4 / rows_mid / rows_lane
+    const int2 *__restrict__ meta_small;
+    const int2 *__restrict__ meta_small4;
+    const int2 *__restrict__ meta_mid;
+    const int2 *__restrict__ meta_lane;
+    const int4 *__restrict__ lane_tab;        // aligned with rows_lane: {v, col0, col1, col2}
     int32_t *cand_small;
     int32_t *cand_mid;
     uint32_t *bitmap;
@@ -103,12 +109,12 @@ struct StepArgs {
     int64_t n_hub_chunks;
     int32_t hub_chunk;
     uint32_t *hub_scratch;          // [n_hubs][Wn*32] per-lane counts (IC: [n_hubs][Wn] masks)
-    unsigned long long *prof_bytes; // [8] algorithmic bytes per kernel kind, or null
+    unsigned long long *prof_bytes; // [FSGP_PROF_KINDS] algorithmic bytes per kind, or null
 };
 
 // profile kinds (fsgp_profile)
 enum { PK_INIT = 0, PK_BEGIN = 1, PK_MARK = 2, PK_HUB = 3, PK_HUBFIN = 4, PK_MID = 5,
-       PK_SMALL = 6, PK_RESULTS = 7 };
+       PK_SMALL = 6, PK_RESULTS = 7, PK_SMALL4 = 8, PK_LANE = 9 };
 
 // Algorithmic bytes of one work item (a slice of `words` words of one row): row pointers,
 // own state read + written, and per gathered in-arc the column index plus the source's

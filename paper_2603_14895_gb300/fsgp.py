@@ -35,14 +35,17 @@ class fsgp_params(ctypes.Structure):
                 ("ic_mode", ctypes.c_int32), ("ic_p", ctypes.c_double)]
 
 
+PROF_KINDS = 10
+
+
 class fsgp_profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64 * 8), ("ms", ctypes.c_double * 8),
-                ("alg_bytes", ctypes.c_double * 8), ("dense_steps", ctypes.c_int64),
+    _fields_ = [("launches", ctypes.c_int64 * PROF_KINDS), ("ms", ctypes.c_double * PROF_KINDS),
+                ("alg_bytes", ctypes.c_double * PROF_KINDS), ("dense_steps", ctypes.c_int64),
                 ("sparse_steps", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
 
 
 PROFILE_KINDS = ["init", "step_control", "frontier_mark", "hub_chunks", "hub_finalize",
-                 "rows_warp", "rows_team", "results"]
+                 "rows_warp", "rows_team", "results", "rows_team4", "rows_lane"]
 
 
 class fsgp_options(ctypes.Structure):
