@@ -235,7 +235,28 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
             else
                 gather_arcs<MODEL, V, B>(A, beg, end, 4, w0, need, ic_thr, x, c, newly);
         }
-        if (WARP_ROW) {
+        constexpr bool SPLIT = WARP_ROW && TPW >= V;   // enough teams to give each word one
+        if constexpr (SPLIT && V == 2 && ModelTraits<MODEL>::counts) {
+            // merge the teams' counters, reduce-scatter first: at the first butterfly level
+            // the partners (teams 2j, 2j+1) swap halves and keep word (team & 1) each, so
+            // the remaining levels add one word instead of two; team i < 2 ends up with
+            // the warp total of word i, which it decides below
+            const int par = team & 1;
+            uint32_t d[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) d[b] = __shfl_xor_sync(0xffffffffu, par ? c[0][b] : c[1][b], TEAM);
+#pragma unroll
+            for (int b = 0; b < B; ++b) c[0][b] = par ? c[1][b] : c[0][b];
+            add_sliced<B>(c[0], d);
+#pragma unroll
+            for (int o = 2 * TEAM; o < 32; o <<= 1) {
+#pragma unroll
+                for (int b = 0; b < B; ++b) d[b] = __shfl_xor_sync(0xffffffffu, c[0][b], o);
+                add_sliced<B>(c[0], d);
+            }
+#pragma unroll
+            for (int b = 0; b < B; ++b) c[1][b] = c[0][b];
+        } else if (WARP_ROW) {
             // merge the teams' partial results (the warp is converged here)
 #pragma unroll
             for (int o = TEAM; o < 32; o <<= 1) {
@@ -254,7 +275,6 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
         }
         uint32_t fl = 0u;
         bool writer;
-        constexpr bool SPLIT = WARP_ROW && TPW >= V;   // enough teams to give each word one
         if constexpr (SPLIT) {
             // every team holds the merged counts of the same words: team i < V decides the
             // i-th word of each thread's V words, so the decisions of a row run V-wide
@@ -443,20 +463,23 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, true>()) k_hub_chunks(Step
                 }
             }
         }
-        if (lane < TEAM) {   // team 0 of the warp holds the warp's totals
+        if constexpr (ModelTraits<MODEL>::counts) {
+            // every team holds the warp's merged counts: the lanes' counts are read out
+            // by all teams, each taking every (32/TEAM)-th lane
+            constexpr int TPW = 32 / TEAM;
 #pragma unroll
             for (int i = 0; i < V; ++i) {
                 const int wsl = w0 + i - ws0;   // word within the slice
-                if constexpr (ModelTraits<MODEL>::counts) {
-                    uint32_t nz = any_count<B>(c[i]);
-                    while (nz) {
-                        const int l = __ffs(nz) - 1;
-                        nz &= nz - 1;
-                        atomicAdd(&s_cnt[wsl * 32 + l], lane_count<B>(c[i], l));
-                    }
-                } else {
-                    if (newly[i]) atomicOr(&s_cnt[wsl], newly[i]);
+                for (int l = team % TPW; l < 32; l += TPW) {
+                    const uint32_t k = lane_count<B>(c[i], l);
+                    if (k) atomicAdd(&s_cnt[wsl * 32 + l], k);
                 }
+            }
+        } else if (lane < TEAM) {   // team 0 of the warp holds the warp's live masks
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const int wsl = w0 + i - ws0;
+                if (newly[i]) atomicOr(&s_cnt[wsl], newly[i]);
             }
         }
         if (A.prof_bytes && threadIdx.x == 0)
