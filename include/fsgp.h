@@ -252,7 +252,7 @@ int fsgp_autotune(const fsgp_graph *g, int32_t model, const fsgp_params *params,
  * The paper has no learned component.  This 3-layer message-passing network predicts
  * each node's probability of being infected by the end of a run from the seed set and
  * (beta, gamma), to screen many candidate seed sets before Monte Carlo re-scores the
- * best; plain Monte Carlo (fsgp_simulate) stays the judge.
+ * best; plain Monte Carlo (fsgp_simulate) makes the final decision.
  *   x_v = [seed_v, beta, gamma, log(1+d_in), log(1+d_out), log(1+k_v), 0, 0], k_v = in-arcs
  *         of v from seeds (a seed listed twice counts twice)
  *   h'_v = ReLU(h_v Ws_l + mean_{u->v} h_u Wn_l + b_l), l = 1..3, width 64
