@@ -644,6 +644,7 @@ __global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
         const bool has = item < nitems;
         int32_t v = 0, beg = 0, d = 0;
         int w0 = 0;
+        uint32_t busy = 0u;
         if (has) {
             const int64_t r = item / nsl;
             w0 = (int)(item - r * nsl) * SWL;
@@ -653,31 +654,64 @@ __global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
             d = (e.y >= 0) + (e.z >= 0) + (e.w >= 0);
             if (MODEL == FSGP_IC) beg = __ldg(&A.meta_lane[r].x);   // arc positions key the draws
             const size_t off = (size_t)v * A.Wn + w0;
-            // own words and sources' words, 4 (or fewer) words per load
+            // own words and sources' words, 4 (or fewer) words per load; bit i of `busy`
+            // records whether some lane of word i can change at this step (an infected
+            // lane to recover, or a lane that can change with a set source lane in its
+            // in-arcs)
 #pragma unroll
             for (int q = 0; q < SWL; q += (SWL < 4 ? SWL : 4)) {
                 constexpr int VL = SWL < 4 ? SWL : 4;
                 const Vec<VL> a = ldg_vec<VL>(A.cur + off + q);
                 Vec<VL> bb{};
                 if (P == 2) bb = ldg_vec<VL>(A.cur + A.plane_words + off + q);
+                uint32_t xs[VL];
 #pragma unroll
                 for (int i = 0; i < VL; ++i) {
                     st.v[0][q + i][tid] = a.w[i];
                     st.v[1][q + i][tid] = P == 2 ? bb.w[i] : 0u;
+                    xs[i] = 0u;
                 }
 #pragma unroll
                 for (int j = 0; j < kLaneMaxDeg; ++j) {
                     Vec<VL> x{};
                     if (u[j] >= 0) x = ldg_vec<VL>(src_plane + (size_t)u[j] * A.Wn + w0 + q);
 #pragma unroll
-                    for (int i = 0; i < VL; ++i) st.v[2 + j][q + i][tid] = x.w[i];
+                    for (int i = 0; i < VL; ++i) {
+                        st.v[2 + j][q + i][tid] = x.w[i];
+                        xs[i] |= x.w[i];
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < VL; ++i) {
+                    const uint32_t s0 = a.w[i], s1 = P == 2 ? bb.w[i] : 0u;
+                    const uint32_t act = (MODEL == FSGP_SIR || MODEL == FSGP_SIS)
+                                             ? (s0 | (~s0 & ~s1 & xs[i]))
+                                             : (s1 | (~s0 & xs[i]));   // IC/LT: F clears, or lanes activate
+                    if (act) busy |= 1u << (q + i);
                 }
             }
         }
         uint32_t fl = 0u;
-        if (has) {
+        if (has && !busy) {
+            // no lane can change: the next state is this one
+            const size_t off = (size_t)v * A.Wn + w0;
+#pragma unroll
+            for (int q = 0; q < SWL; q += (SWL < 4 ? SWL : 4)) {
+                constexpr int VL = SWL < 4 ? SWL : 4;
+                uint32_t n0[VL], n1[VL];
+#pragma unroll
+                for (int i = 0; i < VL; ++i) {
+                    n0[i] = st.v[0][q + i][tid];
+                    n1[i] = st.v[1][q + i][tid];
+                }
+                st_vec<VL>(A.nxt + off + q, n0);
+                if (P == 2) st_vec<VL>(A.nxt + A.plane_words + off + q, n1);
+            }
+        } else if (has) {
+            // only the words in which some lane can change; the others keep their state
 #pragma unroll 1
-            for (int i = 0; i < SWL; ++i) {
+            for (uint32_t bw = busy; bw; bw &= bw - 1u) {
+                const int i = __ffs(bw) - 1;
                 const WordCtx x = word_ctx(A, w0 + i);
                 const uint32_t s0 = st.v[0][i][tid], s1 = st.v[1][i][tid];
                 const uint32_t x0 = st.v[2][i][tid], x1 = st.v[3][i][tid], x2 = st.v[4][i][tid];
