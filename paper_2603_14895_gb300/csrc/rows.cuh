@@ -654,10 +654,9 @@ __global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
             d = (e.y >= 0) + (e.z >= 0) + (e.w >= 0);
             if (MODEL == FSGP_IC) beg = __ldg(&A.meta_lane[r].x);   // arc positions key the draws
             const size_t off = (size_t)v * A.Wn + w0;
-            // own words and sources' words, 4 (or fewer) words per load; bit i of `busy`
-            // records whether some lane of word i can change at this step (an infected
-            // lane to recover, or a lane that can change with a set source lane in its
-            // in-arcs)
+            // own words and sources' words, 4 (or fewer) words per load; `busy` records
+            // whether any lane can change at this step (an infected lane to recover, or a
+            // lane that can change with a set source lane in its in-arcs)
 #pragma unroll
             for (int q = 0; q < SWL; q += (SWL < 4 ? SWL : 4)) {
                 constexpr int VL = SWL < 4 ? SWL : 4;
@@ -684,10 +683,8 @@ __global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
 #pragma unroll
                 for (int i = 0; i < VL; ++i) {
                     const uint32_t s0 = a.w[i], s1 = P == 2 ? bb.w[i] : 0u;
-                    const uint32_t act = (MODEL == FSGP_SIR || MODEL == FSGP_SIS)
-                                             ? (s0 | (~s0 & ~s1 & xs[i]))
-                                             : (s1 | (~s0 & xs[i]));   // IC/LT: F clears, or lanes activate
-                    if (act) busy |= 1u << (q + i);
+                    if (MODEL == FSGP_SIR || MODEL == FSGP_SIS) busy |= s0 | (~s0 & ~s1 & xs[i]);
+                    else busy |= s1 | (~s0 & xs[i]);   // IC/LT: the F plane clears, or lanes activate
                 }
             }
         }
@@ -708,10 +705,8 @@ __global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
                 if (P == 2) st_vec<VL>(A.nxt + A.plane_words + off + q, n1);
             }
         } else if (has) {
-            // only the words in which some lane can change; the others keep their state
 #pragma unroll 1
-            for (uint32_t bw = busy; bw; bw &= bw - 1u) {
-                const int i = __ffs(bw) - 1;
+            for (int i = 0; i < SWL; ++i) {
                 const WordCtx x = word_ctx(A, w0 + i);
                 const uint32_t s0 = st.v[0][i][tid], s1 = st.v[1][i][tid];
                 const uint32_t x0 = st.v[2][i][tid], x1 = st.v[3][i][tid], x2 = st.v[4][i][tid];
