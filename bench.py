@@ -126,13 +126,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+PROPAGATION_SOURCES = ("fsgp_internal.cuh", "step.cuh", "rows.cuh", "model_sir.cu", "model_sis.cu",
+                       "model_ic.cu", "model_lt.cu", "simulate.cu", "graph.cu")
+
+
 def kernel_source_hash() -> str:
+    """Hash of the sources of the propagation kernels (the ones the traffic figures cover)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2603_14895_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    for f in PROPAGATION_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
