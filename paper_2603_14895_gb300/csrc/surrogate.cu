@@ -900,20 +900,20 @@ extern "C" int fsgp_surrogate_screen(fsgp_surrogate *s, const fsgp_graph *g, con
     // ordered after the caller's work
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
-    FSGP_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    FSGP_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    FSGP_CUDA(cudaEventRecord(ev, caller));
-    FSGP_CUDA(cudaStreamWaitEvent(st, ev, 0));
     int32_t *d_cand = nullptr;
     float *d_scores = nullptr;
-    FSGP_CUDA(cudaMalloc(&d_cand, sizeof(int32_t) * (size_t)k * n_cand));
-    cudaError_t e = cudaMalloc(&d_scores, sizeof(float) * (size_t)n_cand);
-    if (e != cudaSuccess) {
-        cudaFree(d_cand);
-        return cuda_fail(e, "cudaMalloc (screen)");
-    }
+    cudaError_t e;
     rc = FSGP_OK;
     do {
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventRecord(ev, caller)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(st, ev, 0)) != cudaSuccess ||
+            (e = cudaMalloc(&d_cand, sizeof(int32_t) * (size_t)k * n_cand)) != cudaSuccess ||
+            (e = cudaMalloc(&d_scores, sizeof(float) * (size_t)n_cand)) != cudaSuccess) {
+            rc = cuda_fail(e, "screen setup");
+            break;
+        }
         if ((e = cudaMemcpyAsync(d_cand, cand_host, sizeof(int32_t) * (size_t)k * n_cand, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
             (e = cudaMemsetAsync(d_scores, 0, sizeof(float) * (size_t)n_cand, st)) != cudaSuccess ||
             (e = cudaMemsetAsync(s->cur, 0, sizeof(int32_t), st)) != cudaSuccess) {
@@ -952,7 +952,7 @@ extern "C" int fsgp_surrogate_screen(fsgp_surrogate *s, const fsgp_graph *g, con
     } while (0);
     cudaFree(d_cand);
     cudaFree(d_scores);
-    cudaEventDestroy(ev);
-    cudaStreamDestroy(st);
+    if (ev) cudaEventDestroy(ev);
+    if (st) cudaStreamDestroy(st);
     return rc;
 }
