@@ -278,6 +278,78 @@ def run_batch_bench(args):
             "clocks": clocks}
 
 
+# ------------------------------------------------------- the smaller workloads
+
+def run_config_bench(args, which: str):
+    """Throughput on the other benchmark configurations (one bench step = one full run of
+    every model of the configuration; units are the edge-realization-steps computed,
+    IC/LT stopping at quiescence):
+      ba1m:  BA n=1,000,000 m=5 (both directions), IC weighted cascade and LT, 50 seeds,
+             R=1024, T<=100 to quiescence.
+      er10k: ER n=10,000 mean degree 10, SIR beta=0.05 gamma=0.1, 1% seeds, R=64, T=50;
+             the step loop is captured in a CUDA graph (launch-bound size)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2603_14895_gb300 import fsgp
+    torch.cuda.set_device(0)
+    if which == "ba1m":
+        g = W.ba1m_graph()
+        wls = [W.ba1m(W.IC, g), W.ba1m(W.LT, g)]
+        opts = {}
+    else:
+        wls = [W.er10k_sir()]
+        g = wls[0].graph
+        opts = {"capture_graph": 1}
+    graph = fsgp.Graph(g.row_ptr, g.col_idx)
+    stream = torch.cuda.Stream()
+    outs = []
+    with torch.cuda.stream(stream):
+        for wl in wls:
+            outs.append(fsgp.simulate(graph, wl.model, wl.seed_sets, wl.R, wl.T, wl.rng_seed,
+                                      beta=wl.beta, gamma=wl.gamma, ic_mode=wl.ic_mode, ic_p=wl.ic_p,
+                                      freq=True, options=dict(opts), stream=stream))
+
+    def step():
+        for wl, o in zip(wls, outs):
+            fsgp.simulate(graph, wl.model, wl.seed_sets, wl.R, wl.T, wl.rng_seed, beta=wl.beta,
+                          gamma=wl.gamma, ic_mode=wl.ic_mode, ic_p=wl.ic_p, freq=True,
+                          options=dict(opts), stream=stream, out=o)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_selector(torch))
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(1, args.steps)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(reps):
+            step()
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / reps
+    units = 0.0
+    per_model = {}
+    for wl, o in zip(wls, outs):
+        st = int(o["steps_run"][0].item())
+        u = float(g.nnz) * wl.R * st
+        units += u
+        per_model[wl.name] = {"steps_run": st, "edge_realization_steps": u}
+    name = "ba1m_ic_lt_R1024" if which == "ba1m" else "er10k_sir_R64_T50"
+    return {"metric": "edge-realization-steps/sec", "value": units / (ms / 1e3),
+            "unit": "edge-realization-steps/s", "n_gpus": 1, "steps": reps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": name, "n": g.n, "nnz": g.nnz, "models": per_model,
+                       "l2": "state and graph fit in L2 for er10k; ba1m exceeds it; no flush"},
+            "realization_runs_per_s": sum(wl.R for wl in wls) / (ms / 1e3),
+            "clocks": clocks}
+
+
 # -------------------------------------------------------------- learned surrogate
 
 SG_R, SG_T, SG_GAMMA, SG_K = 1024, 100, 0.1, 20
@@ -471,7 +543,7 @@ def main():
     ap.add_argument("--scale", type=int, default=SCALE)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="rmat26", choices=["rmat26", "batch", "surrogate"])
+    ap.add_argument("--workload", default="rmat26", choices=["rmat26", "batch", "surrogate", "ba1m", "er10k"])
     ap.add_argument("--sg-graphs", type=int, default=200)
     ap.add_argument("--sg-epochs", type=int, default=6)
     ap.add_argument("--sg-lr", type=float, default=2e-3)
@@ -494,6 +566,9 @@ def main():
         return
     if args.workload == "surrogate" and args.impl == "fsgp":
         print(json.dumps(run_surrogate_bench(args)), flush=True)
+        return
+    if args.workload in ("ba1m", "er10k") and args.impl == "fsgp":
+        print(json.dumps(run_config_bench(args, args.workload)), flush=True)
         return
 
     if args.impl == "reference":
