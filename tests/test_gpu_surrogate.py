@@ -164,6 +164,7 @@ def test_training_and_screening_gain(cuda_lib):
     rank_m = np.argsort(np.argsort(mc))
     spearman = np.corrcoef(rank_s, rank_m)[0, 1]
     info = (mc[top].mean(), mc[rand].mean(), mc.mean(), mc.std(), spearman)
+    print("top-10 MC mean, random-10 MC mean, all mean, all std, Spearman:", info)
     assert mc[top].mean() > mc[rand].mean(), info
     # chance level: about 0 with a standard deviation of 1/sqrt(119) = 0.09
     assert spearman > 0.5, info
