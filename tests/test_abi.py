@@ -61,3 +61,31 @@ def test_product_path_does_not_touch_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets gcc gives the
+    C structure of include/fsgp.h (a mismatch would pass garbage through the ABI)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    from paper_2603_14895_gb300 import fsgp
+    structs = ["fsgp_params", "fsgp_profile", "fsgp_options", "fsgp_result", "fsgp_request",
+               "fsgp_batch_options"]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fsgp.h"', "int main(void) {"]
+    expect = []
+    for sname in structs:
+        cls = getattr(fsgp, sname)
+        lines.append(f'    printf("%zu\\n", sizeof({sname}));')
+        expect.append(ctypes.sizeof(cls))
+        for fname, _ in cls._fields_:
+            lines.append(f'    printf("%zu\\n", offsetof({sname}, {fname}));')
+            expect.append(getattr(cls, fname).offset)
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).decode().split()]
+    assert got == expect
