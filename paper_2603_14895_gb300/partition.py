@@ -65,15 +65,16 @@ def partition_graph(row_ptr, col_idx, d: int, q=None) -> list[Partition]:
         q = target_partition(deg, d)
     parts = []
     for p in range(d):
-        t = np.nonzero(q == p)[0].astype(np.int32)
+        in_p = q == p
+        t = np.nonzero(in_p)[0].astype(np.int32)
         dt = deg[t]
         rp = np.zeros(t.shape[0] + 1, dtype=np.int64)
         np.cumsum(dt, out=rp[1:])
-        begin = row_ptr[t]
-        # gather each target's arc range in order
-        idx = (np.repeat(begin - rp[:-1], dt) + np.arange(int(rp[-1]), dtype=np.int64)) if rp[-1] else \
-            np.zeros(0, dtype=np.int64)
-        cols = col_idx[idx]
+        # the arcs of this partition's rows, in CSR order (rows are contiguous arc ranges)
+        cols = col_idx[np.repeat(in_p, deg)]
+        seen = np.zeros(deg.shape[0], dtype=bool)   # distinct sources by marking, not sorting
+        seen[cols] = True
         parts.append(Partition(targets=t, row_ptr=rp.astype(np.int32), col_idx=cols,
-                               arc_begin=begin.astype(np.int64), sources=np.unique(cols)))
+                               arc_begin=row_ptr[t].astype(np.int64),
+                               sources=np.nonzero(seen)[0].astype(np.int32)))
     return parts
