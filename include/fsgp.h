@@ -58,7 +58,7 @@ extern "C" {
 #define FSGP_ENOMEM (-2)          /* device or host allocation failed */
 #define FSGP_ECUDA (-3)           /* a CUDA runtime call failed (message has details) */
 #define FSGP_ETIMEOUT (-4)        /* a bounded device-side wait ran out */
-#define FSGP_EUNSUPPORTED (-5)    /* a valid request this build does not implement */
+#define FSGP_EUNSUPPORTED (-5)    /* a valid request this library version does not implement */
 
 /* ------------------------------------------------------------------------ models */
 #define FSGP_SIR 0   /* planes: 0 = I (infected), 1 = R (recovered) */

@@ -9,9 +9,9 @@ messages; after each step the partitions' new target states are combined (one su
 partitions, every node contributed by exactly one of them).  The load of every
 partition is within w_max of W / d.
 
-Host logic only (numpy).  One device holds the graphs this build targets (the R-MAT
-scale-26 stand-in needs 10.7 GB of 288), so the propagation kernels run unpartitioned;
-this module is the partitioner and its subgraph extraction.
+Host logic only (numpy).  One GB300 holds graphs of a billion arcs (an R-MAT scale-26
+graph with its tables takes 10.7 GB of 288), so the propagation kernels run
+unpartitioned; this module is the partitioner and its subgraph extraction.
 """
 from __future__ import annotations
 
