@@ -58,3 +58,20 @@ def test_seed_sets():
     assert s.min() >= 0 and s.max() < 1000
     assert np.array_equal(s, W.seed_set(1000, 100, seed=5))
     assert not np.array_equal(s, W.seed_set(1000, 100, seed=6))
+
+
+def test_surrogate_pool_and_candidates_are_seeded_and_shaped():
+    import numpy as np
+    import workloads as W
+    gs = W.surrogate_pool(4, n_min=2000, n_max=4000, threads=2)
+    gs2 = W.surrogate_pool(4, n_min=2000, n_max=4000, threads=1)
+    for a, b in zip(gs, gs2):          # a pure function of the seed, not of the thread count
+        assert np.array_equal(a.row_ptr, b.row_ptr) and np.array_equal(a.col_idx, b.col_idx)
+    assert gs[0].name.startswith("ba") and gs[1].name.startswith("rmat")
+    assert 2000 <= gs[0].n <= 4000 and gs[1].n in (1 << 17, 1 << 18, 1 << 19)
+    sets = W.surrogate_sets(gs[0], 0)
+    assert len(sets) == 8 and all(len(s) == 20 and 0.01 <= b <= 0.1 for s, b in sets)
+    c = W.surrogate_candidates(gs[0], 50, 20, seed=3)
+    assert c.shape == (50, 20) and c.dtype == np.int32
+    assert c.min() >= 0 and c.max() < gs[0].n
+    assert np.array_equal(c, W.surrogate_candidates(gs[0], 50, 20, seed=3))
