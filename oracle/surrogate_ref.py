@@ -11,13 +11,15 @@ Definition (restated here, computed in float64):
   p_v   = sigmoid(h3_v . w_o + b_o)
   loss  = mean_v (p_v - y_v)^2,  y_v = fraction of realizations in which v was infected
 
-The GPU feeds its tensor-core products with bfloat16 operands (weights, inputs,
-activations, aggregated means, and in the backward pass the pre-activation gradients dz)
-and accumulates in float32.  With `bf16=True` this reference rounds exactly those
-operands to bfloat16 (round to nearest even) and keeps everything else in float64 (the
-bias gradient sums the unrounded dz), so the two differ only by float32 accumulation
-order.  With `bf16=False` it is the plain float64 function, whose analytic gradients the
-tests check against finite differences.
+With `bf16=False` this is the plain float64 function, whose analytic gradients the tests
+check against finite differences.  Evaluated on bfloat16-rounded weights and inputs (the
+operands the network is given on the GPU), it is the reference the GPU's forward pass and
+gradients are held to, within tolerances derived from the bfloat16 unit roundoff.
+
+With `bf16=True` it additionally rounds the intermediate operands that the GPU rounds
+before its tensor-core products (activations, aggregated means, and in the backward pass
+the pre-activation gradients dz; round to nearest even).  That variant only serves as a
+diagnostic: it separates accumulation-order differences from rounding differences.
 """
 from __future__ import annotations
 

@@ -1,5 +1,19 @@
 """Learned surrogate on the GPU (through the C ABI) against the float64 CPU reference:
-forward probabilities, gradients, training, and what screening gains over no screening."""
+forward probabilities, gradients, training, and what screening gains over no screening.
+
+The reference is the plain float64 network evaluated on the bfloat16-rounded weights and
+inputs (the operands the GPU is given), with no rounding of intermediate values: the
+GPU's own roundings of activations, means and backward pre-activation gradients are
+errors measured against it, not copied into it.  Tolerances, from the bfloat16 unit
+roundoff u = 2^-9 (8 significant bits, round to nearest):
+  - forward: each of the 3 layers rounds its activations and its means once (2u of
+    relative perturbation per layer, at most 6u = 1.2e-2 in the logit); the sigmoid's
+    slope is at most 1/4, so |p_gpu - p| <= 1e-2 per node, and the norm-wise relative
+    error ||p_gpu - p|| / ||p|| <= 1e-2;
+  - backward: the pre-activation gradient is rounded once more per layer (3u more),
+    about 9u = 1.8e-2 relative per gradient block, so <= 2e-2 per block.
+A second, tighter comparison against the reference that rounds the same intermediates
+as the GPU (bf16=True) is kept as a diagnostic of accumulation order only."""
 import numpy as np
 import pytest
 
@@ -7,6 +21,47 @@ import workloads as W
 from oracle import surrogate_ref as S
 
 pytestmark = pytest.mark.gpu
+
+P_ABS_TOL = 1e-2     # per node, forward
+P_REL_TOL = 1e-2     # norm-wise, forward
+G_BLOCK_TOL = 2e-2   # norm-wise, per gradient block
+
+
+def _rounded_operands(theta, x):
+    """The GPU's operands: bfloat16-rounded weights (biases stay float32) and inputs."""
+    th = np.asarray(theta, dtype=np.float64).copy()
+    o = 0
+    for name, shp in S.SHAPES:
+        k = int(np.prod(shp))
+        if not name.startswith("b"):
+            th[o:o + k] = S.bf16_round(th[o:o + k])
+        o += k
+    return th, S.bf16_round(x)
+
+
+def _check_forward(p, theta, g, x):
+    th, xr = _rounded_operands(theta, x)
+    ref, _ = S.forward(th, g.row_ptr, g.col_idx, xr, bf16=False)
+    err = np.abs(p - ref)
+    assert err.max() <= P_ABS_TOL, err.max()
+    assert np.linalg.norm(p - ref) <= P_REL_TOL * np.linalg.norm(ref)
+    diag, _ = S.forward(np.asarray(theta, np.float64), g.row_ptr, g.col_idx, x, bf16=True)
+    assert np.abs(p - diag).max() <= 1e-2
+
+
+def _check_grad(loss, grad, theta, g, x, y):
+    th, xr = _rounded_operands(theta, x)
+    rl, rg = S.loss_and_grad(th, g.row_ptr, g.col_idx, xr, y.astype(np.float64), bf16=False)
+    assert abs(loss - rl) <= 1e-3 * abs(rl), (loss, rl)
+    o = 0
+    for name, shp in S.SHAPES:
+        k = int(np.prod(shp))
+        a, b = grad[o:o + k], rg[o:o + k]
+        assert np.linalg.norm(a - b) <= G_BLOCK_TOL * np.linalg.norm(b) + 1e-7, name
+        o += k
+    _, dg = S.loss_and_grad(np.asarray(theta, np.float64), g.row_ptr, g.col_idx, x,
+                            y.astype(np.float64), bf16=True)
+    assert np.linalg.norm(grad - dg) <= 2e-2 * np.linalg.norm(dg)
 
 
 def _setup(f, n=2500, m=3, seed=401):
@@ -24,10 +79,7 @@ def test_forward_matches_reference(cuda_lib):
     seeds = W.seed_set(g.n, 12, seed=402)
     p = sg.forward(graph, seeds, 0.06, 0.1).cpu().numpy()
     x = S.features(g.row_ptr, g.col_idx, seeds, 0.06, 0.1)
-    ref, _ = S.forward(theta.astype(np.float64), g.row_ptr, g.col_idx, x, bf16=True)
-    err = np.abs(p - ref)
-    assert err.max() <= 1e-2, err.max()
-    assert err.mean() <= 1e-3, err.mean()
+    _check_forward(p, theta, g, x)
     assert np.array_equal(sg.get_params(), theta)
 
 
@@ -42,18 +94,7 @@ def test_gradient_matches_reference(cuda_lib):
     y = np.random.default_rng(7).random(g.n).astype(np.float32)
     loss, grad = sg.grad(graph, seeds, 0.05, 0.1, torch.from_numpy(y).cuda())
     x = S.features(g.row_ptr, g.col_idx, seeds, 0.05, 0.1)
-    rl, rg = S.loss_and_grad(theta.astype(np.float64), g.row_ptr, g.col_idx, x, y.astype(np.float64),
-                             bf16=True)
-    assert abs(loss - rl) <= 1e-3 * abs(rl), (loss, rl)
-    rel = np.linalg.norm(grad - rg) / np.linalg.norm(rg)
-    assert rel <= 2e-2, rel
-    # every block of the gradient, not just the norm
-    o = 0
-    for name, shp in S.SHAPES:
-        k = int(np.prod(shp))
-        a, b = grad[o:o + k], rg[o:o + k]
-        assert np.linalg.norm(a - b) <= 5e-2 * np.linalg.norm(b) + 1e-7, name
-        o += k
+    _check_grad(loss, grad, theta, g, x, y)
 
 
 def _hub_graphs():
@@ -85,15 +126,10 @@ def test_long_rows_forward_and_gradient(cuda_lib, gi):
     seeds = np.array([0, int(np.argmax(dout)), 5, 9], dtype=np.int32)
     p = sg.forward(graph, seeds, 0.05, 0.1).cpu().numpy()
     x = S.features(g.row_ptr, g.col_idx, seeds, 0.05, 0.1)
-    ref, _ = S.forward(theta.astype(np.float64), g.row_ptr, g.col_idx, x, bf16=True)
-    err = np.abs(p - ref)
-    assert err.max() <= 1e-2 and err.mean() <= 1e-3, (err.max(), err.mean())
+    _check_forward(p, theta, g, x)
     y = np.random.default_rng(3).random(g.n).astype(np.float32)
     loss, grad = sg.grad(graph, seeds, 0.05, 0.1, torch.from_numpy(y).cuda())
-    rl, rg = S.loss_and_grad(theta.astype(np.float64), g.row_ptr, g.col_idx, x, y.astype(np.float64),
-                             bf16=True)
-    assert abs(loss - rl) <= 1e-3 * abs(rl)
-    assert np.linalg.norm(grad - rg) <= 2e-2 * np.linalg.norm(rg)
+    _check_grad(loss, grad, theta, g, x, y)
     # a second call reuses the graph's cleared accumulators: same result
     p2 = sg.forward(graph, seeds, 0.05, 0.1).cpu().numpy()
     assert np.abs(p2 - p).max() <= 5e-3   # float32 atomics may reorder a sum
