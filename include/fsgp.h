@@ -57,7 +57,7 @@ extern "C" {
 #define FSGP_EINVAL (-1)          /* an argument is out of range or inconsistent */
 #define FSGP_ENOMEM (-2)          /* device or host allocation failed */
 #define FSGP_ECUDA (-3)           /* a CUDA runtime call failed (message has details) */
-#define FSGP_ETIMEOUT (-4)        /* a bounded device-side wait ran out */
+/* (-4) is not used: no kernel of this library waits on another CTA or device */
 #define FSGP_EUNSUPPORTED (-5)    /* a valid request this library version does not implement */
 
 /* ------------------------------------------------------------------------ models */
@@ -290,10 +290,10 @@ int fsgp_surrogate_screen(fsgp_surrogate *s, const fsgp_graph *g, const int32_t 
                           void *stream);
 
 /* One synchronous step (Eq. nodestate) of `model` that allocates no device memory.
- * The paper has no counterpart: this entry point exists for callers that cannot call
- * cudaMalloc -- code running inside a stream capture or a pre-built CUDA graph, a
- * process that has handed its free device memory to its own pool, or a runtime that
- * forbids allocation on its hot path.  It needs no graph handle.
+ * The paper has no counterpart.  It serves callers that cannot call cudaMalloc: a
+ * process that has handed its free device memory to its own pool up front (a serving
+ * process with a fixed memory budget), or an embedding runtime that forbids device
+ * allocation on its hot path.  It needs no graph handle.
  *   row_ptr, col_idx: device in-CSR as for fsgp_graph_create (not validated here).
  *   cur_planes: device input state, next_planes: device output state (must not alias),
  *     both [planes][n][Ws] u32 with Ws = the smallest power of two >= ceil(R/32);
@@ -307,11 +307,13 @@ int fsgp_surrogate_screen(fsgp_surrogate *s, const fsgp_graph *g, const int32_t 
  * GPU that loads the library until the process exits.  Limits, checked before any
  * work (EINVAL with a message): n * 128 * Ws bytes plus about 1.1 MB of tables must fit
  * the 32 MiB; for SIR/SIS the in-degree may not exceed 65536 unless the survival table
- * reaches zero earlier (beta not tiny).  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) and caches it: make that first call
- * before any stream capture.  Every call shares the array and clears it; calls that
- * overlap on the GPU race, so order them (one stream, or events).  The call reads the
- * chunk count back and therefore synchronises `stream` once.  Errors: EINVAL, ECUDA. */
+ * reaches zero earlier (beta not tiny).  The first call on a device, with that device
+ * current, looks up the array's device address (cudaGetSymbolAddress) and keeps it for
+ * the process: make that first call before any stream capture.  A device reset
+ * (cudaDeviceReset) invalidates the kept address, so do not call this entry point after
+ * one.  Every call shares the array and clears the part it uses; calls that overlap on
+ * the GPU race, so order them (one stream, or events).  The call reads the chunk count
+ * back to the host and therefore synchronises `stream` once.  Errors: EINVAL, ECUDA. */
 int fsgp_step_noalloc(int32_t model, const fsgp_params *params, const int32_t *row_ptr,
                       const int32_t *col_idx, int32_t n, int64_t nnz, int32_t R, uint32_t t,
                       uint64_t rng_seed, const uint32_t *cur_planes, uint32_t *next_planes,

@@ -1,10 +1,10 @@
 // noalloc.cu -- fsgp_step_noalloc: one synchronous propagation step that allocates no
 // device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs inside a CUDA stream capture or a
-// pre-built CUDA graph, code whose memory is fully budgeted up front (a serving process
-// that has handed all free device memory to its own pool), or an embedding runtime that
-// forbids allocation on its hot path.  For them this entry point computes one dense step
+// Some callers cannot call cudaMalloc: code whose memory is fully budgeted up front (a
+// serving process that has handed all free device memory to its own pool), or an
+// embedding runtime that forbids allocation on its hot path.  For them this entry point
+// computes one dense step
 // of SIR, SIS, IC or LT over a graph and state planes that the caller already holds in
 // device memory, with every row taking the CTA-split path of the hub rows: each row's
 // in-arcs are cut into chunks, one CTA per chunk adds per-lane counts (IC: live lanes)
@@ -44,7 +44,9 @@ constexpr size_t kOffRows = kOffSurv + a256(sizeof(uint64_t) * (kSurvCap + 1));
 std::mutex g_mu;
 void *g_ptr[256] = {};
 
-// Device address of the scratch on the current device, looked up once per device.
+// Device address of the scratch on the current device, looked up once per device (the
+// first call on a device, with it current) and kept for the process; a device reset
+// invalidates it.
 int noalloc_scratch(int dev, char **out) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (dev < 0 || dev >= 256) return fail(FSGP_EINVAL, "device ordinal out of range");
@@ -240,8 +242,9 @@ extern "C" int fsgp_step_noalloc(int32_t model, const fsgp_params *params, const
     const int TEAM = SW / V;
 
     StepArgs A{};
-    A.row_ptr = row_ptr;
+    A.rp = row_ptr;        // rows are the caller's nodes: no relabelling (orig, pos null)
     A.col = col_idx;
+    A.arc0 = row_ptr;      // IC arc keys: the caller's arc positions
     A.out_ptr = row_ptr;   // read only for frontier bookkeeping, which this step discards
     A.out_dst = nullptr;
     A.n = n;
@@ -260,7 +263,6 @@ extern "C" int fsgp_step_noalloc(int32_t model, const fsgp_params *params, const
     A.k = 1;
     A.ctl = ctl;
     A.pc = pc;
-    A.hub_rows = rows;
     A.hub_chunk_base = chunk_base;
     A.n_hubs = n;
     A.n_hub_chunks = n_chunks;
