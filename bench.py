@@ -15,6 +15,12 @@ region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fsgp|reference]
 
+With --gpus N > 1 and no torchrun environment (WORLD_SIZE unset), bench.py starts the N
+ranks itself (torch.distributed.run on 127.0.0.1, one process per GPU) and exits with
+their status; under torchrun it is one of the ranks.  --dry-run checks the launch: every
+rank joins the process group (NCCL with GPUs, gloo without), takes its realization shard,
+and rank 0 prints the ranks' lane ranges; nothing is simulated.
+
 --impl reference times the CPU oracle (test infrastructure) on a bounded sample of the
 same workload: the paper's method has no runnable reference implementation here.
 Multi-GPU (torchrun): realization sharding, rank i runs lanes with r_offset = 256 i
@@ -531,6 +537,51 @@ def run_surrogate_bench(args):
             "clocks": clocks}
 
 
+# ----------------------------------------------------------------- multi-rank launch
+
+def _free_port() -> int:
+    import socket
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as so:
+        so.bind(("127.0.0.1", 0))
+        return so.getsockname()[1]
+
+
+def launch_ranks(n: int, argv) -> int:
+    """Start n ranks of this script under torch.distributed.run on this node (rendezvous
+    on 127.0.0.1) and return their exit status."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
+           os.path.abspath(__file__), *argv]
+    log(f"[bench] starting {n} ranks: {' '.join(cmd[1:6])} ...")
+    return subprocess.call(cmd, cwd=ROOT)
+
+
+def dry_run(args, world: int, rank: int, local: int) -> dict | None:
+    """Join the process group, take this rank's realization shard, gather the shards on
+    rank 0.  No simulation."""
+    import torch
+    import torch.distributed as dist
+    from paper_2603_14895_gb300.shard import lane_shard
+    use_nccl = torch.cuda.is_available() and torch.cuda.device_count() > local
+    if world > 1:
+        if use_nccl:
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
+    r0, rl = lane_shard(R * world, world, rank)
+    mine = {"rank": rank, "local_rank": local, "r_offset": r0, "R": rl}
+    shards = [mine]
+    if world > 1:
+        shards = [None] * world
+        dist.all_gather_object(shards, mine)
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    return {"dry_run": True, "n_gpus": world, "backend": ("nccl" if use_nccl else "gloo") if world > 1 else None,
+            "lanes_per_rank": R, "ranks": shards}
+
+
 # ------------------------------------------------------------------------- main
 
 def main():
@@ -554,12 +605,20 @@ def main():
     ap.add_argument("--single-reps", type=int, default=2)
     ap.add_argument("--batch-graphs", type=int, default=64)
     ap.add_argument("--batch-requests", type=int, default=4096)
+    ap.add_argument("--dry-run", action="store_true")
     args = ap.parse_args()
     SCALE = args.scale
 
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(launch_ranks(args.gpus, sys.argv[1:]))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.dry_run:
+        out = dry_run(args, world, rank, local)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
 
     if args.workload == "batch" and args.impl == "fsgp":
         print(json.dumps(run_batch_bench(args)), flush=True)
@@ -600,6 +659,10 @@ def main():
     log(f"[bench] graph on device in {time.time() - t0:.1f}s: {graph.info()}")
     from paper_2603_14895_gb300.shard import lane_shard
     r_offset, _ = lane_shard(R * world, world, rank)     # weak scaling: R lanes per rank
+    shards = [{"rank": rank, "r_offset": r_offset, "R": R}]
+    if dist is not None:
+        shards = [None] * world
+        dist.all_gather_object(shards, {"rank": rank, "r_offset": r_offset, "R": R})
     stream = torch.cuda.current_stream()
     outs = {m: fsgp.simulate(graph, m, [seeds], R, T, RNG_SEED, beta=BETA, gamma=GAMMA,
                              freq=True, device=True,
@@ -740,6 +803,7 @@ def main():
         "e2e": e2e,
         "single_instance": single,
         "gpu_launches": int(launches),
+        "ranks": shards,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(g, seeds)
