@@ -87,8 +87,7 @@ struct HubTable {
     int32_t chunk = -1;
     int32_t n_hubs = 0;
     int64_t n_chunks = 0;
-    int32_t *d_rows = nullptr;        // [n_hubs], aliases the head of rows_sorted (not owned)
-    int64_t *d_chunk_base = nullptr;  // [n_hubs + 1]
+    int64_t *d_chunk_base = nullptr;  // [n_hubs + 1] (hub rows are new ids 0 .. n_hubs-1)
 };
 
 struct Workspace {
@@ -128,10 +127,21 @@ struct fsgp_graph {
     int32_t *out_ptr = nullptr;     // [n+1] out-CSR
     int32_t *out_dst = nullptr;     // [nnz]
     int32_t *rows_sorted = nullptr; // [n] rows by degree bucket, high buckets first
-    int2 *row_meta = nullptr;       // [n] {row_ptr[v], row_ptr[v+1]} of rows_sorted[i]
-    int4 *lane_tab = nullptr;       // rows with at most 3 in-arcs (the tail of rows_sorted
-                                    // from bucket 2 on): {v, col0, col1, col2}, -1 = none
-    int32_t lane_start = 0;         // index in rows_sorted of lane_tab[0]
+    // The propagation kernels work on the rows relabelled in rows_sorted order: row i of
+    // the state planes is node rows_sorted[i] ("new id" i), so the rows of one degree
+    // class are one contiguous range and the most-read sources (high-degree nodes) sit
+    // together at the front of every plane.
+    int32_t *pos = nullptr;         // [n] new id of each node (inverse of rows_sorted)
+    int32_t *rp2 = nullptr;         // [n+1] in-CSR row pointers in new-id order
+    int32_t *col2 = nullptr;        // [nnz] sources as new ids, rows in new-id order (each
+                                    // row's arcs in their original order)
+    int32_t *arc0 = nullptr;        // [n] position in col of the first arc of new row i
+                                    // (IC draws are keyed by the original arc position)
+    int4 *lane_tab = nullptr;       // new rows with 1..3 in-arcs (from bucket 2 to the
+                                    // start of bucket 0): {node, src0, src1, src2}, sources
+                                    // as new ids, -1 = none
+    int32_t lane_start = 0;         // new id of lane_tab[0]
+    int32_t d0_start = 0;           // new id of the first row without in-arcs
     fsgp::ClassInfo cls{};
     fsgp::HubTable hub{};
     fsgp::Workspace ws{};

@@ -247,23 +247,41 @@ int exclusive_scan_i32(const int32_t *in, int64_t n, int32_t *out, int64_t *tile
     return FSGP_OK;
 }
 
-// Row pointers of the rows in bucket order, so the row kernels read a row's arc range
-// from a coalesced array instead of a random pair of row_ptr entries.
-__global__ void k_row_meta(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ rows, int32_t n,
-                           int2 *meta) {
+// Relabelling (new id i = position of node rows_sorted[i]): inverse map, per-row in-degree
+// in new order (scanned into rp2 afterwards) and the original position of each row's first
+// arc.
+__global__ void k_relabel_rows(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ rows,
+                               int32_t n, int32_t *pos, int32_t *deg2, int32_t *arc0) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = rows[i];
-        meta[i] = make_int2(row_ptr[v], row_ptr[v + 1]);
+        pos[v] = (int32_t)i;
+        const int32_t b = row_ptr[v];
+        deg2[i] = row_ptr[v + 1] - b;
+        arc0[i] = b;
     }
 }
 
-// Rows with at most 3 in-arcs: the row and its (up to 3) sources in one 16-byte entry.
-__global__ void k_lane_tab(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-                           const int32_t *__restrict__ rows, int32_t count, int4 *tab) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t v = rows[i];
-        const int32_t b = row_ptr[v], d = row_ptr[v + 1] - b;
-        tab[i] = make_int4(v, d > 0 ? col[b] : -1, d > 1 ? col[b + 1] : -1, d > 2 ? col[b + 2] : -1);
+// Sources as new ids, rows in new order (one warp per row; rows of a warp's neighbourhood
+// have similar degrees because new ids follow the degree buckets).
+__global__ void k_relabel_cols(const int32_t *__restrict__ arc0, const int32_t *__restrict__ rp2,
+                               const int32_t *__restrict__ col, const int32_t *__restrict__ pos,
+                               int32_t n, int32_t *col2) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < n; i += n_warps) {
+        const int32_t b = arc0[i], o = rp2[i], d = rp2[i + 1] - o;
+        for (int32_t k = lane; k < d; k += 32) col2[o + k] = pos[col[b + k]];
+    }
+}
+
+// New rows with 1..3 in-arcs: the node and its (up to 3) sources in one 16-byte entry.
+__global__ void k_lane_tab(const int32_t *__restrict__ rp2, const int32_t *__restrict__ col2,
+                           const int32_t *__restrict__ rows, int32_t first, int32_t count, int4 *tab) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < count; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = first + r;
+        const int32_t b = rp2[i], d = rp2[i + 1] - b;
+        tab[r] = make_int4(rows[i], d > 0 ? col2[b] : -1, d > 1 ? col2[b + 1] : -1, d > 2 ? col2[b + 2] : -1);
     }
 }
 
@@ -274,7 +292,10 @@ static void release(fsgp_graph *g) {
     cudaFree(g->out_ptr);
     cudaFree(g->out_dst);
     cudaFree(g->rows_sorted);
-    cudaFree(g->row_meta);
+    cudaFree(g->pos);
+    cudaFree(g->rp2);
+    cudaFree(g->col2);
+    cudaFree(g->arc0);
     cudaFree(g->lane_tab);
     cudaFree(g->hub.d_chunk_base);
     cudaFree(g->ws.ptr);
@@ -443,20 +464,34 @@ extern "C" int fsgp_graph_create(const int32_t *row_ptr, const int32_t *col_idx,
                 break;
             }
         }
-        // bucket-ordered row pointers and the table of rows with at most 3 in-arcs
+        // relabelled in-CSR (new ids in rows_sorted order) and the table of rows with 1..3
+        // in-arcs
         g->lane_start = g->cls.bucket_start[2];
-        const int32_t n_lane = n - g->lane_start;
-        if ((e = cudaMalloc(&g->row_meta, sizeof(int2) * (size_t)n)) != cudaSuccess ||
+        g->d0_start = g->cls.bucket_start[0];
+        const int32_t n_lane = g->d0_start - g->lane_start;
+        if ((e = cudaMalloc(&g->pos, sizeof(int32_t) * (size_t)n)) != cudaSuccess ||
+            (e = cudaMalloc(&g->rp2, rp_bytes)) != cudaSuccess ||
+            (e = cudaMalloc(&g->col2, col_bytes)) != cudaSuccess ||
+            (e = cudaMalloc(&g->arc0, sizeof(int32_t) * (size_t)n)) != cudaSuccess ||
             (n_lane > 0 && (e = cudaMalloc(&g->lane_tab, sizeof(int4) * (size_t)n_lane)) != cudaSuccess)) {
-            rc = cuda_fail(e, "cudaMalloc (row tables)");
+            rc = cuda_fail(e, "cudaMalloc (relabelled graph)");
             break;
         }
-        g->device_bytes += sizeof(int2) * (size_t)n + sizeof(int4) * (size_t)n_lane;
-        k_row_meta<<<grid_for(n, 256, g->sm_count), 256, 0, s>>>(g->row_ptr, g->rows_sorted, n, g->row_meta);
+        g->device_bytes += 2 * sizeof(int32_t) * (size_t)n + rp_bytes + col_bytes + sizeof(int4) * (size_t)n_lane;
+        // d_cnt (n+1 entries) holds the degrees in new order; entry n = 0 ends the scan
+        if ((e = cudaMemsetAsync(d_cnt + n, 0, sizeof(int32_t), s)) != cudaSuccess) {
+            rc = cuda_fail(e, "cudaMemsetAsync");
+            break;
+        }
+        k_relabel_rows<<<grid_for(n, 256, g->sm_count), 256, 0, s>>>(g->row_ptr, g->rows_sorted, n, g->pos,
+                                                                     d_cnt, g->arc0);
+        if ((rc = exclusive_scan_i32(d_cnt, (int64_t)n + 1, g->rp2, d_tiles, s)) != FSGP_OK) break;
+        if (nnz > 0)
+            k_relabel_cols<<<grid_for((int64_t)n * 32, 256, g->sm_count), 256, 0, s>>>(g->arc0, g->rp2, g->col,
+                                                                                      g->pos, n, g->col2);
         if (n_lane > 0)
-            k_lane_tab<<<grid_for(n_lane, 256, g->sm_count), 256, 0, s>>>(g->row_ptr, g->col,
-                                                                          g->rows_sorted + g->lane_start,
-                                                                          n_lane, g->lane_tab);
+            k_lane_tab<<<grid_for(n_lane, 256, g->sm_count), 256, 0, s>>>(g->rp2, g->col2, g->rows_sorted,
+                                                                          g->lane_start, n_lane, g->lane_tab);
         if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess) {
             rc = cuda_fail(e, "graph build kernels");
             break;

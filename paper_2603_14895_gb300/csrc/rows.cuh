@@ -57,9 +57,11 @@ __device__ __forceinline__ uint64_t ic_threshold(const StepArgs &A, int s, int32
 // into bit-sliced counters (SIR/SIS/LT) or live-lane masks (IC).  Software pipelined:
 // the column indices of the next group are loaded while the state words of the current
 // group are in flight, so each group costs one memory latency instead of two.
+// IC draws are keyed by the arc's position in the caller's column array: arc e of the
+// relabelled array is caller arc e + arcb.
 template <int MODEL, int V, int B>
 __device__ __forceinline__ void gather_arcs(const StepArgs &A, int64_t e_begin, int64_t e_end,
-                                            int64_t step, int w0, const uint32_t (&need)[V],
+                                            int64_t step, int64_t arcb, int w0, const uint32_t (&need)[V],
                                             const uint64_t (&ic_thr)[V], const WordCtx (&x)[V],
                                             uint32_t (&c)[V][B], uint32_t (&newly)[V]) {
     const uint32_t *src = A.cur + (size_t)ModelTraits<MODEL>::src_plane * A.plane_words + w0;
@@ -94,7 +96,7 @@ __device__ __forceinline__ void gather_arcs(const StepArgs &A, int64_t e_begin, 
                 for (int i = 0; i < V; ++i) {
                     const uint32_t m = xs[j].w[i] & need[i] & ~newly[i];
                     if (m)
-                        newly[i] |= lanes_u_less(m, ic_thr[i], (uint32_t)(e + j), A.t, x[i].g,
+                        newly[i] |= lanes_u_less(m, ic_thr[i], (uint32_t)(e + j + arcb), A.t, x[i].g,
                                                  TAG_IC_EDGE, x[i].k0, x[i].k1);
                 }
             }
@@ -134,16 +136,15 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
     const Ctl *C = A.ctl;
     if (*(volatile const int32_t *)&C->stop) return;
     const bool sparse = *(volatile const int32_t *)&C->sparse != 0;
-    const int32_t *rows;
-    const int2 *meta = nullptr;   // dense steps: the rows' arc ranges, aligned with rows
+    const int32_t *rows = nullptr;   // frontier steps: candidate rows; dense: a range
+    int32_t r0 = 0;
     int64_t nrows;
     if (sparse) {
         if (which >= 2) return;
         rows = which ? A.cand_mid : A.cand_small;
         nrows = (int64_t)((volatile const uint32_t *)C->cand_n)[which];
     } else {
-        rows = which == 0 ? A.rows_small : which == 1 ? A.rows_mid : A.rows_small4;
-        meta = which == 0 ? A.meta_small : which == 1 ? A.meta_mid : A.meta_small4;
+        r0 = which == 0 ? A.r_small : which == 1 ? A.r_mid : A.r_small4;
         nrows = which == 0 ? A.n_small : which == 1 ? A.n_mid : A.n_small4;
     }
     if (nrows == 0) return;
@@ -176,7 +177,8 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
         const bool has_row = item < nitems;
         const int64_t ridx = has_row ? item / A.nslices : 0;
         const int slice = has_row ? (int)(item - ridx * A.nslices) : 0;
-        const int32_t v = has_row ? __ldg(rows + ridx) : 0;
+        const int32_t v = has_row ? (rows ? __ldg(rows + ridx) : r0 + (int32_t)ridx) : 0;   // new id
+        const uint32_t node = has_row ? node_of(A, v) : 0u;                                  // Philox subject
         const int w0 = slice * SW + tl * V;
         const size_t off = (size_t)v * A.Wn + w0;
         if (slice != ctx_slice) {
@@ -216,24 +218,20 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
         }
         int32_t beg = 0, end = 0;
         if (has_row) {
-            if (meta) {
-                const int2 m = __ldg(meta + ridx);
-                beg = m.x;
-                end = m.y;
-            } else {
-                beg = __ldg(A.row_ptr + v);
-                end = __ldg(A.row_ptr + v + 1);
-            }
+            beg = __ldg(A.rp + v);
+            end = __ldg(A.rp + v + 1);
         }
         if (any_need) {
             uint64_t ic_thr[V];
+            int64_t arcb = 0;
+            if constexpr (!ModelTraits<MODEL>::counts) arcb = (int64_t)__ldg(A.arc0 + v) - beg;
 #pragma unroll
             for (int i = 0; i < V; ++i)
                 ic_thr[i] = ModelTraits<MODEL>::counts ? 0ull : ic_threshold(A, x[i].s, end - beg);
             if (WARP_ROW)
-                gather_arcs<MODEL, V, B>(A, (int64_t)beg + 4 * team, end, 4 * TPW, w0, need, ic_thr, x, c, newly);
+                gather_arcs<MODEL, V, B>(A, (int64_t)beg + 4 * team, end, 4 * TPW, arcb, w0, need, ic_thr, x, c, newly);
             else
-                gather_arcs<MODEL, V, B>(A, beg, end, 4, w0, need, ic_thr, x, c, newly);
+                gather_arcs<MODEL, V, B>(A, beg, end, 4, arcb, w0, need, ic_thr, x, c, newly);
         }
         constexpr bool SPLIT = WARP_ROW && TPW >= V;   // enough teams to give each word one
         if constexpr (SPLIT && V == 2 && ModelTraits<MODEL>::counts) {
@@ -298,12 +296,12 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
                 const uint32_t s1 = P == 2 ? __ldg(A.cur + A.plane_words + off + i) : 0u;
                 WordOut o;
                 if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SIS) {
-                    o = update_sir_word<MODEL, B>(A, (uint32_t)v, xw, s0, s1, end - beg, cw);
+                    o = update_sir_word<MODEL, B>(A, node, xw, s0, s1, end - beg, cw);
                 } else if constexpr (MODEL == FSGP_IC) {
                     o.n0 = s0 | nw;
                     o.n1 = nw;
                 } else {
-                    o = update_lt_word<B>(A, (uint32_t)v, xw, s0, end - beg, cw);
+                    o = update_lt_word<B>(A, node, xw, s0, end - beg, cw);
                 }
                 A.nxt[off + i] = o.n0;
                 if (P == 2) A.nxt[A.plane_words + off + i] = o.n1;
@@ -344,12 +342,12 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
             for (int i = 0; i < V; ++i) {
                 WordOut o;
                 if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SIS) {
-                    o = update_sir_word<MODEL, B>(A, (uint32_t)v, x[i], s0[i], s1[i], end - beg, c[i]);
+                    o = update_sir_word<MODEL, B>(A, node, x[i], s0[i], s1[i], end - beg, c[i]);
                 } else if constexpr (MODEL == FSGP_IC) {
                     o.n0 = s0[i] | newly[i];
                     o.n1 = newly[i];
                 } else {
-                    o = update_lt_word<B>(A, (uint32_t)v, x[i], s0[i], end - beg, c[i]);
+                    o = update_lt_word<B>(A, node, x[i], s0[i], end - beg, c[i]);
                 }
                 n0[i] = o.n0;
                 n1[i] = o.n1;
@@ -370,7 +368,7 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
         }
         const bool leader = writer && tl == 0;
         const bool want = leader && fl != 0u;
-        if (want && (fl & 1u)) acc.push_deg += (unsigned long long)(__ldg(A.out_ptr + v + 1) - __ldg(A.out_ptr + v));
+        if (want && (fl & 1u)) acc.push_deg += (unsigned long long)(__ldg(A.out_ptr + node + 1) - __ldg(A.out_ptr + node));
         if (A.prof_bytes && leader) acc.bytes += row_bytes(SW, P, any_need != 0u, end - beg);
         list_append(A, build, want, (int32_t)((uint32_t)v | ((fl & 1u) ? kPushBit : 0u)), list_slot);
         if (sparse && leader) atomicAnd(&A.bitmap[v >> 5], ~(1u << (v & 31)));
@@ -412,7 +410,7 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, true>()) k_hub_chunks(Step
             if (__ldg(A.hub_chunk_base + mid) <= item) lo = mid; else hi = mid - 1;
         }
         const int h = lo;
-        const int32_t v = __ldg(A.hub_rows + h);
+        const int32_t v = h;   // hub rows are new ids 0 .. n_hubs-1
         if (sparse && !((A.bitmap[v >> 5] >> (v & 31)) & 1u)) continue;
         const int ws0 = slice * SW;        // first word of the slice
         const int w0 = ws0 + tl * V;
@@ -434,7 +432,9 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, true>()) k_hub_chunks(Step
 #pragma unroll
         for (int o = 1; o < TEAM; o <<= 1) any_need |= __shfl_xor_sync(0xffffffffu, any_need, o);
         if (!any_need) continue;   // identical in every team: they share the slice
-        const int32_t rb = __ldg(A.row_ptr + v), re = __ldg(A.row_ptr + v + 1);
+        const int32_t rb = __ldg(A.rp + v), re = __ldg(A.rp + v + 1);
+        int64_t arcb = 0;
+        if constexpr (!ModelTraits<MODEL>::counts) arcb = (int64_t)__ldg(A.arc0 + v) - rb;
         const int64_t cidx = item - __ldg(A.hub_chunk_base + h);
         const int64_t beg = (int64_t)rb + cidx * A.hub_chunk;
         const int64_t end = min((int64_t)re, beg + A.hub_chunk);
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, true>()) k_hub_chunks(Step
 #pragma unroll
             for (int b = 0; b < B; ++b) c[i][b] = 0u;
         }
-        gather_arcs<MODEL, V, B>(A, beg + 4 * team, end, 4 * TPB, w0, need, ic_thr, x, c, newly);
+        gather_arcs<MODEL, V, B>(A, beg + 4 * team, end, 4 * TPB, arcb, w0, need, ic_thr, x, c, newly);
 #pragma unroll
         for (int o = TEAM; o < 32; o <<= 1) {
 #pragma unroll
@@ -529,11 +529,12 @@ __global__ void __launch_bounds__(kBlock) k_hub_finalize(StepArgs A) {
     const int list_slot = A.k & 1;
     Accum acc;
     for (int64_t h = gwarp; h < A.n_hubs; h += nwarps) {
-        const int32_t v = __ldg(A.hub_rows + h);
+        const int32_t v = (int32_t)h;
+        const uint32_t node = node_of(A, v);
         const bool cand = !sparse || ((A.bitmap[v >> 5] >> (v & 31)) & 1u);
         uint32_t fl = 0u;
         if (cand) {
-            const int32_t d = __ldg(A.row_ptr + v + 1) - __ldg(A.row_ptr + v);
+            const int32_t d = __ldg(A.rp + v + 1) - __ldg(A.rp + v);
             uint32_t *slot = A.hub_scratch + (size_t)h * nl;
             for (int g0 = 0; g0 < A.Wn; g0 += 32) {
                 const int w = g0 + lane;
@@ -566,13 +567,13 @@ __global__ void __launch_bounds__(kBlock) k_hub_finalize(StepArgs A) {
                     const WordCtx x = word_ctx(A, w);
                     WordOut o;
                     if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SIS) {
-                        o = update_sir_word<MODEL, 32>(A, (uint32_t)v, x, s0, s1, d, c);
+                        o = update_sir_word<MODEL, 32>(A, node, x, s0, s1, d, c);
                     } else if constexpr (MODEL == FSGP_IC) {
                         const uint32_t nw2 = newly & x.vm & ~s0;
                         o.n0 = s0 | nw2;
                         o.n1 = nw2;
                     } else {
-                        o = update_lt_word<32>(A, (uint32_t)v, x, s0, d, c);
+                        o = update_lt_word<32>(A, node, x, s0, d, c);
                     }
                     A.nxt[off] = o.n0;
                     if (P == 2) A.nxt[A.plane_words + off] = o.n1;
@@ -590,7 +591,7 @@ __global__ void __launch_bounds__(kBlock) k_hub_finalize(StepArgs A) {
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) fl |= __shfl_xor_sync(0xffffffffu, fl, o);
         const bool want = cand && lane == 0 && fl != 0u;
-        if (want && (fl & 1u)) acc.push_deg += (unsigned long long)(__ldg(A.out_ptr + v + 1) - __ldg(A.out_ptr + v));
+        if (want && (fl & 1u)) acc.push_deg += (unsigned long long)(__ldg(A.out_ptr + node + 1) - __ldg(A.out_ptr + node));
         if (A.prof_bytes && cand && lane == 0)
             acc.bytes += row_bytes(A.Wn, P, false, 0) + 2ull * 4ull * 32ull * (unsigned long long)A.Wn;
         list_append(A, build, want, (int32_t)((uint32_t)v | ((fl & 1u) ? kPushBit : 0u)), list_slot);
@@ -601,8 +602,11 @@ __global__ void __launch_bounds__(kBlock) k_hub_finalize(StepArgs A) {
     if (lanes_on) flush_lanes(A, s_lane, nl);
 }
 
-// Rows with at most 3 in-arcs (including none), dense steps only (on frontier steps
-// such rows come through the candidate lists of k_rows).  Most rows of a power-law graph
+// Rows with 1..3 in-arcs, and the rows without in-arcs whose state can change (listed by
+// the step-0 scan: seeds, or imported rows with infected / newly active lanes; every
+// other row without in-arcs keeps its state for the whole run and is never touched),
+// dense steps only (on frontier steps such rows come through the candidate lists of
+// k_rows).  Most rows of a power-law graph
 // are of this kind and carry little gather work, so the cost is the chain of dependent
 // loads per row: one THREAD per item (a slice of SWL <= 8 words of one row) keeps four
 // to eight times as many rows in flight per SM as a team per row.  The thread loads its
@@ -625,7 +629,8 @@ __global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
     if (*(volatile const int32_t *)&C->stop) return;
     if (*(volatile const int32_t *)&C->sparse) return;
     const int nsl = A.Wn / SWL;
-    const int64_t nitems = (int64_t)A.n_lane * nsl;
+    const int64_t n_rows = (int64_t)A.n_lane + *(volatile const uint32_t *)&C->d0_n;
+    const int64_t nitems = n_rows * nsl;
     if (nitems == 0) return;
     const int nl = A.Wn * 32;
     const bool lanes_on = A.lane_cnt != nullptr;
@@ -642,17 +647,25 @@ __global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
     for (int64_t item = (int64_t)blockIdx.x * blockDim.x + tid; item - tid < nitems;
          item += (int64_t)gridDim.x * blockDim.x) {
         const bool has = item < nitems;
-        int32_t v = 0, beg = 0, d = 0;
+        int32_t v = 0, beg = 0, d = 0;   // v: new id
+        uint32_t node = 0u;              // Philox subject
         int w0 = 0;
         uint32_t busy = 0u;
         if (has) {
             const int64_t r = item / nsl;
             w0 = (int)(item - r * nsl) * SWL;
-            const int4 e = __ldg(A.lane_tab + r);   // the row and its sources in one entry
-            v = e.x;
+            int4 e;
+            if (r < A.n_lane) {
+                e = __ldg(A.lane_tab + r);   // the node and its sources in one entry
+                v = A.r_lane + (int32_t)r;
+            } else {
+                v = A.d0_list[r - A.n_lane];
+                e = make_int4((int32_t)node_of(A, v), -1, -1, -1);
+            }
+            node = (uint32_t)e.x;
             const int32_t u[kLaneMaxDeg] = {e.y, e.z, e.w};
             d = (e.y >= 0) + (e.z >= 0) + (e.w >= 0);
-            if (MODEL == FSGP_IC) beg = __ldg(&A.meta_lane[r].x);   // arc positions key the draws
+            if (MODEL == FSGP_IC && d > 0) beg = __ldg(A.arc0 + v);   // arc positions key the draws
             const size_t off = (size_t)v * A.Wn + w0;
             // own words and sources' words, 4 (or fewer) words per load; `busy` records
             // whether any lane can change at this step (an infected lane to recover, or a
@@ -732,12 +745,12 @@ __global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
                         const uint32_t need = x.vm & ~s0;
                         c[0] &= need;
                         c[1] &= need;
-                        o = update_lt_word<2>(A, (uint32_t)v, x, s0, d, c);
+                        o = update_lt_word<2>(A, node, x, s0, d, c);
                     } else {
                         const uint32_t need = x.vm & ~s0 & ~s1;
                         c[0] &= need;
                         c[1] &= need;
-                        o = update_sir_word<MODEL, 2>(A, (uint32_t)v, x, s0, s1, d, c);
+                        o = update_sir_word<MODEL, 2>(A, node, x, s0, s1, d, c);
                     }
                 }
                 st.v[0][i][tid] = o.n0;
@@ -771,7 +784,7 @@ __global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
             }
         }
         const bool want = has && fl != 0u;
-        if (want && (fl & 1u)) acc.push_deg += (unsigned long long)(__ldg(A.out_ptr + v + 1) - __ldg(A.out_ptr + v));
+        if (want && (fl & 1u)) acc.push_deg += (unsigned long long)(__ldg(A.out_ptr + node + 1) - __ldg(A.out_ptr + node));
         if (A.prof_bytes && has) acc.bytes += row_bytes(SWL, P, d > 0, d);
         list_append(A, build, want, (int32_t)((uint32_t)v | ((fl & 1u) ? kPushBit : 0u)), list_slot);
     }
@@ -796,8 +809,10 @@ int launch_rows_lane(const StepArgs &A, int swl, int grid, size_t smem, cudaStre
 template <int MODEL, int SWL>
 int occupancy_lane_w(size_t smem) {
     // the staging area is static; per-lane counters (dynamic) may push the total past the
-    // default 48 KB window (set before any launch or capture)
-    cudaFuncSetAttribute(k_rows_lane<MODEL, SWL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // default 48 KB window.  The attribute is process-wide and host threads of a batch set
+    // it concurrently, so it is always raised to the largest per-lane counter area any run
+    // uses (32 KB), never lowered to this run's need (set before any launch or capture).
+    cudaFuncSetAttribute(k_rows_lane<MODEL, SWL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * 1024);
     int z = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&z, k_rows_lane<MODEL, SWL>, kBlock, smem);
     return z;

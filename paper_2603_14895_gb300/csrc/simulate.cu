@@ -32,16 +32,17 @@ struct SetOut {
 
 // ------------------------------------------------------------------------ kernels
 
-// Seed nodes of one set: all valid lanes of its source planes, in both buffers.
+// Seed nodes of one set: all valid lanes of its source planes, in both buffers (rows are
+// new ids: node v is row pos[v]).
 __global__ void k_seed(uint32_t *buf0, uint32_t *buf1, size_t plane_words, int both_planes,
-                       const int32_t *__restrict__ seeds, int64_t ns, int Wn, int ws0, int Ws,
-                       int W, uint32_t last_mask) {
+                       const int32_t *__restrict__ seeds, int64_t ns, const int32_t *__restrict__ pos,
+                       int Wn, int ws0, int Ws, int W, uint32_t last_mask) {
     const int64_t total = ns * Ws;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t si = i / Ws;
         const int w = (int)(i % Ws);
-        const int32_t v = seeds[si];
+        const int32_t v = pos[seeds[si]];
         const uint32_t m = w < W - 1 ? 0xffffffffu : (w == W - 1 ? last_mask : 0u);
         const size_t off = (size_t)v * Wn + ws0 + w;
         buf0[off] = m;
@@ -53,26 +54,31 @@ __global__ void k_seed(uint32_t *buf0, uint32_t *buf1, size_t plane_words, int b
     }
 }
 
-// Caller-supplied start planes of one set [planes][n][W] -> both buffers.
+// Caller-supplied start planes of one set [planes][n][W] (node order) -> both buffers
+// (row order).
 __global__ void k_import(const uint32_t *__restrict__ in, int planes, int32_t n, int W, int Ws,
-                         int Wn, int ws0, uint32_t last_mask, uint32_t *buf0, uint32_t *buf1) {
+                         int Wn, int ws0, uint32_t last_mask, const int32_t *__restrict__ pos,
+                         uint32_t *buf0, uint32_t *buf1) {
     const int64_t total = (int64_t)planes * n * Ws;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int w = (int)(i % Ws);
-        const int64_t pv = i / Ws;   // plane * n + v
+        const int64_t pv = i / Ws;   // plane * n + node
+        const int64_t p = pv / n, v = pv - p * n;
         uint32_t x = 0u;
         if (w < W) {
             x = in[pv * W + w];
             if (w == W - 1) x &= last_mask;
         }
-        const size_t o = (size_t)pv * Wn + ws0 + w;
+        const size_t o = ((size_t)p * n + (size_t)pos[v]) * Wn + ws0 + w;
         buf0[o] = x;
         buf1[o] = x;
     }
 }
 
-// Step-0 totals per set, per-lane counts and the rows whose source lanes push at step 1.
+// Step-0 totals per set, per-lane counts, the rows whose source lanes push at step 1, and
+// the rows without in-arcs whose state can change (those that push: an infected lane can
+// recover, a newly active lane stops being new), which dense steps visit through d0_list.
 __global__ void __launch_bounds__(kBlock) k_init_scan(StepArgs A, int model) {
     extern __shared__ int32_t s_lane[];
     __shared__ unsigned long long s_pc[2 * kMaxSets];
@@ -104,9 +110,23 @@ __global__ void __launch_bounds__(kBlock) k_init_scan(StepArgs A, int model) {
                 push |= (model == FSGP_SIR || model == FSGP_SIS) ? (s0 != 0u) : (s1 != 0u);
             }
         }
-        if (push) acc.push_deg += (unsigned long long)(A.out_ptr[v + 1] - A.out_ptr[v]);
+        if (push) {
+            const uint32_t node = node_of(A, (int32_t)v);
+            acc.push_deg += (unsigned long long)(A.out_ptr[node + 1] - A.out_ptr[node]);
+        }
         if (has && A.prof_bytes) acc.bytes += (two ? 2ull : 1ull) * 4ull * (unsigned long long)A.Wn;
         list_append(A, build, has && push, (int32_t)((uint32_t)v | kPushBit), 0);
+        {
+            const bool d0 = has && push && v >= A.r_d0;
+            const unsigned m = __ballot_sync(0xffffffffu, d0);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                uint32_t b = 0;
+                if (lane == leader) b = atomicAdd(&A.ctl->d0_n, (uint32_t)__popc(m));
+                b = __shfl_sync(0xffffffffu, b, leader);
+                if (d0) A.d0_list[b + __popc(m & ((1u << lane) - 1u))] = (int32_t)v;
+            }
+        }
     }
     flush_accum(A, acc, 0, PK_INIT);
     set_acc_flush(A, s_pc);
@@ -183,7 +203,7 @@ __device__ __forceinline__ void mark_round(const StepArgs &A, int32_t x) {
         const uint32_t bit = 1u << (x & 31);
         const uint32_t old = atomicOr(&A.bitmap[x >> 5], bit);
         if (!(old & bit)) {
-            const int32_t d = __ldg(A.row_ptr + x + 1) - __ldg(A.row_ptr + x);
+            const int32_t d = __ldg(A.rp + x + 1) - __ldg(A.rp + x);
             if (d < A.hub_min_deg) cls = d > A.small_max_deg ? 1 : 0;
         }
     }
@@ -212,9 +232,10 @@ __global__ void __launch_bounds__(kBlock) k_mark(StepArgs A) {
         const int32_t v = (int32_t)(entry & ~kPushBit);
         mark_round(A, lane == 0 ? v : -1);
         if (entry & kPushBit) {
-            const int32_t b = __ldg(A.out_ptr + v), e = __ldg(A.out_ptr + v + 1);
+            const uint32_t node = node_of(A, v);   // out-arcs are listed by node
+            const int32_t b = __ldg(A.out_ptr + node), e = __ldg(A.out_ptr + node + 1);
             for (int32_t j = b; j < e; j += 32) {
-                const int32_t x = j + lane < e ? __ldg(A.out_dst + j + lane) : -1;
+                const int32_t x = j + lane < e ? row_of(A, __ldg(A.out_dst + j + lane)) : -1;
                 mark_round(A, x);
             }
         }
@@ -256,15 +277,16 @@ __global__ void k_freq(StepArgs A, int model, const uint32_t *buf0, const uint32
                        const SetOut *outs) {
     const uint32_t *st = (A.ctl->steps_done & 1) ? buf1 : buf0;
     const bool two = model != FSGP_SIS;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < A.n;
-         v += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = node_of(A, (int32_t)i);   // row i holds node v
         for (int s = 0; s < A.S; ++s) {
             uint32_t *fr = outs[s].freq;
             if (!fr) continue;
             const int W = A.sp[s].W;
             int64_t p0 = 0, p1 = 0;
             for (int w = 0; w < W; ++w) {
-                const size_t off = (size_t)v * A.Wn + (size_t)s * A.Ws + w;
+                const size_t off = (size_t)i * A.Wn + (size_t)s * A.Ws + w;
                 p0 += __popc(st[off]);
                 if (two) p1 += __popc(st[A.plane_words + off]);
             }
@@ -277,7 +299,7 @@ __global__ void k_freq(StepArgs A, int model, const uint32_t *buf0, const uint32
     }
 }
 
-// Final planes of one set -> caller layout [planes][n][W].
+// Final planes of one set -> caller layout [planes][n][W] in node order.
 __global__ void k_export(StepArgs A, int planes, int ws0, int W, const uint32_t *buf0,
                          const uint32_t *buf1, uint32_t *out) {
     const uint32_t *st = (A.ctl->steps_done & 1) ? buf1 : buf0;
@@ -285,8 +307,9 @@ __global__ void k_export(StepArgs A, int planes, int ws0, int W, const uint32_t 
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int w = (int)(i % W);
-        const int64_t pv = i / W;
-        out[i] = st[(size_t)pv * A.Wn + ws0 + w];
+        const int64_t pv = i / W;   // plane * n + node
+        const int64_t p = pv / A.n, v = pv - p * A.n;
+        out[i] = st[((size_t)p * A.n + (size_t)row_of(A, (int32_t)v)) * A.Wn + ws0 + w];
     }
 }
 
@@ -325,7 +348,6 @@ static int ensure_hub_table(fsgp_graph *g, int hub_min_deg, int chunk, cudaStrea
     const int32_t n_hubs = bh >= 1 ? g->cls.bucket_start[bh - 1] : g->n;
     cudaFree(H.d_chunk_base);
     H.d_chunk_base = nullptr;
-    H.d_rows = nullptr;
     H.n_hubs = n_hubs;
     H.n_chunks = 0;
     H.min_deg = hub_min_deg;
@@ -347,7 +369,6 @@ static int ensure_hub_table(fsgp_graph *g, int hub_min_deg, int chunk, cudaStrea
     FSGP_CUDA(cudaMemcpyAsync(H.d_chunk_base, base.data(), sizeof(int64_t) * base.size(),
                               cudaMemcpyHostToDevice, s));
     FSGP_CUDA(cudaStreamSynchronize(s));
-    H.d_rows = g->rows_sorted;
     H.n_chunks = base[n_hubs];
     return FSGP_OK;
 }
@@ -454,11 +475,14 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     const int32_t start_mid = bh >= 1 ? g->cls.bucket_start[bh - 1] : n;
     const int32_t start_small = g->cls.bucket_start[bs];
     const int32_t n_mid = start_small - start_mid;
-    // small rows by in-degree class; rows_sorted holds the buckets in descending order
-    // (bucket b: 2^(b-1) <= d < 2^b, bucket 0: d = 0), so each class is one range
-    const int32_t start_lane = std::max(bs >= 2 ? g->cls.bucket_start[2] : start_small, start_small);  // d 0..3
+    // small rows by in-degree class; new ids follow the buckets in descending order
+    // (bucket b: 2^(b-1) <= d < 2^b, bucket 0: d = 0), so each class is one range; rows
+    // without in-arcs (from d0_start on) are only visited through the d0 list
+    const int32_t start_lane = std::max(bs >= 2 ? g->cls.bucket_start[2] : start_small, start_small);  // d 1..3
     const int32_t start_small4 = bs >= 4 ? g->cls.bucket_start[4] : start_small;   // d 4..15
-    const int32_t n_lane = n - start_lane;
+    const int32_t d0_start = g->d0_start;
+    const int32_t n_lane = std::max(0, d0_start - start_lane);
+    const int32_t n_d0 = n - d0_start;
     const int32_t n_small4 = start_lane - std::max(start_small4, start_small);
     const int32_t n_small = std::max(start_small4, start_small) - start_small;        // d 16..small_max
     const int32_t n_small_all = n - start_small;
@@ -497,7 +521,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     const size_t state_words = (size_t)P * n * Wn;
     enum { O_STATE, O_PC, O_CTL, O_LIST0, O_LIST1, O_CSMALL, O_CMID, O_BITMAP, O_LANES,
            O_HUB, O_SURV, O_SEEDS, O_COUNTS, O_FREQ, O_PREAL, O_PLANES, O_PROF, O_SP, O_OUT,
-           O_STEPS, O_END };
+           O_STEPS, O_D0, O_END };
     size_t sz[O_END] = {0};
     sz[O_STATE] = 2 * state_words * sizeof(uint32_t);
     sz[O_PC] = T1 * S * 2 * sizeof(unsigned long long);
@@ -518,6 +542,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     sz[O_SP] = (size_t)S * sizeof(SetParams);
     sz[O_OUT] = (size_t)S * sizeof(SetOut);
     sz[O_STEPS] = (size_t)S * sizeof(int32_t);
+    sz[O_D0] = (size_t)n_d0 * sizeof(int32_t);
     size_t off[O_END], total = 0;
     for (int i = 0; i < O_END; ++i) {
         off[i] = total;
@@ -577,13 +602,13 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     // the 16..small_max kernel also takes every small row of a frontier step
     L.have_small = n_small_all > 0;
     L.have_small4 = n_small4 > 0;
-    L.have_lane = n_lane > 0;
+    L.have_lane = n_lane > 0 || n_d0 > 0;
     L.swl = occ.swl;
     L.have_mid = n_mid > 0;
     L.have_hub = n_hubs > 0;
     L.prof = profiling ? &prof : nullptr;
     const int64_t items_small = (int64_t)n_small_all * nslices, items_mid = (int64_t)n_mid * nslices;
-    const int64_t items_lane = (int64_t)n_lane * (Wn / occ.swl);
+    const int64_t items_lane = (int64_t)(n_lane + n_d0) * (Wn / occ.swl);
     const int per_block_small = (kBlock / 32) * (32 / TEAM);
     auto grid_for_items = [&](int per_sm, int64_t items) {
         return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * per_sm,
@@ -603,8 +628,11 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     const int grid_scan = grid_cap((int64_t)n, kBlock, g->sm_count, 8);
 
     StepArgs A{};
-    A.row_ptr = g->row_ptr;
-    A.col = g->col;
+    A.rp = g->rp2;
+    A.col = g->col2;
+    A.orig = g->rows_sorted;
+    A.pos = g->pos;
+    A.arc0 = g->arc0;
     A.out_ptr = g->out_ptr;
     A.out_dst = g->out_dst;
     A.n = n;
@@ -621,23 +649,20 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     A.ic_mode = ic_mode;
     A.ctl = ctl;
     A.lane_cnt = want_lanes ? (int32_t *)(ws + off[O_LANES]) : nullptr;
-    A.rows_small = g->rows_sorted + start_small;
-    A.rows_small4 = g->rows_sorted + std::max(start_small4, start_small);
-    A.rows_lane = g->rows_sorted + start_lane;
-    A.meta_small = g->row_meta + start_small;
-    A.meta_small4 = g->row_meta + std::max(start_small4, start_small);
-    A.meta_mid = g->row_meta + start_mid;
-    A.meta_lane = g->row_meta + start_lane;
-    A.lane_tab = g->lane_tab ? g->lane_tab + (start_lane - g->lane_start) : nullptr;
-    A.n_lane = n_lane;
-    A.n_small4 = n_small4;
-    A.rows_mid = g->rows_sorted + start_mid;
+    A.r_small = start_small;
     A.n_small = n_small;
+    A.r_small4 = std::max(start_small4, start_small);
+    A.n_small4 = n_small4;
+    A.r_lane = start_lane;
+    A.n_lane = n_lane;
+    A.r_mid = start_mid;
     A.n_mid = n_mid;
+    A.r_d0 = d0_start;
+    A.lane_tab = (g->lane_tab && n_lane > 0) ? g->lane_tab + (start_lane - g->lane_start) : nullptr;
+    A.d0_list = (int32_t *)(ws + off[O_D0]);
     A.cand_small = (int32_t *)(ws + off[O_CSMALL]);
     A.cand_mid = (int32_t *)(ws + off[O_CMID]);
     A.bitmap = (uint32_t *)(ws + off[O_BITMAP]);
-    A.hub_rows = g->hub.d_rows;
     A.hub_chunk_base = g->hub.d_chunk_base;
     A.n_hubs = n_hubs;
     A.n_hub_chunks = g->hub.n_chunks;
@@ -672,7 +697,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
                 src = stage;
             }
             k_import<<<grid_cap((int64_t)P * n * Ws, 256, g->sm_count, 16), 256, 0, s>>>(
-                src, P, n, hp[i].W, Ws, Wn, ws0, hp[i].last_mask, buf0, buf1);
+                src, P, n, hp[i].W, Ws, Wn, ws0, hp[i].last_mask, g->pos, buf0, buf1);
             ++launches;
         } else if (x.n_seeds > 0) {
             const int32_t *sd = x.seeds;
@@ -684,7 +709,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
             }
             k_seed<<<grid_cap(x.n_seeds * Ws, 256, g->sm_count, 16), 256, 0, s>>>(
                 buf0, buf1, A.plane_words, model != FSGP_SIR && model != FSGP_SIS, sd, x.n_seeds,
-                Wn, ws0, Ws, hp[i].W, hp[i].last_mask);
+                g->pos, Wn, ws0, Ws, hp[i].W, hp[i].last_mask);
             ++launches;
         }
     }

@@ -42,6 +42,7 @@ struct Ctl {
     int32_t sparse_steps;  // steps run on the frontier lists
     int32_t build_list;    // the current step lists its rows for the next step
     int32_t list_valid[2]; // the list of that parity was built
+    uint32_t d0_n;         // rows without in-arcs listed by the step-0 scan (d0_list)
 };
 
 // Per-set parameters (device array, one entry per set of the launch).
@@ -56,11 +57,18 @@ struct SetParams {
     uint64_t p_const;               // IC constant threshold
 };
 
+// Row ids are "new ids": the graph's rows relabelled in degree-bucket order (row i of
+// the state planes is node orig[i]).  Random draws are keyed by the node (Philox subject)
+// and, for IC, by the arc's position in the caller's column array, so relabelling changes
+// no result bit.  A null orig / pos means the identity (callers without a graph handle).
 struct StepArgs {
-    // graph
-    const int32_t *__restrict__ row_ptr;
-    const int32_t *__restrict__ col;
-    const int32_t *__restrict__ out_ptr;
+    // graph, new ids
+    const int32_t *__restrict__ rp;      // [n+1] in-CSR row pointers
+    const int32_t *__restrict__ col;     // [nnz] sources
+    const int32_t *__restrict__ orig;    // [n] node of new row i, or null
+    const int32_t *__restrict__ pos;     // [n] new id of node v, or null
+    const int32_t *__restrict__ arc0;    // [n] caller's position of new row i's first arc
+    const int32_t *__restrict__ out_ptr; // caller's out-CSR (nodes), frontier marking
     const int32_t *__restrict__ out_dst;
     int32_t n;
     int32_t Ws;            // words per set (power of two)
@@ -84,26 +92,19 @@ struct StepArgs {
     Ctl *ctl;
     unsigned long long *pc;        // [S][2] plane popcounts of this step (running totals)
     int32_t *lane_cnt;             // [2][Wn*32] running per-lane plane counts, or null
-    // row lists
-    // dense steps: small rows by in-degree class (16.., 4..15, 0..3), mid rows
-    const int32_t *__restrict__ rows_small;
-    const int32_t *__restrict__ rows_small4;
-    const int32_t *__restrict__ rows_lane;
-    const int32_t *__restrict__ rows_mid;
-    int32_t n_small, n_small4, n_lane, n_mid;
-    // {row_ptr[v], row_ptr[v+1]} aligned with rows_small / rows_small4 / rows_mid / rows_lane
-    const int2 *__restrict__ meta_small;
-    const int2 *__restrict__ meta_small4;
-    const int2 *__restrict__ meta_mid;
-    const int2 *__restrict__ meta_lane;
-    const int4 *__restrict__ lane_tab;        // aligned with rows_lane: {v, col0, col1, col2}
+    // dense steps: row classes as new-id ranges: small rows by in-degree class (16..,
+    // 4..15, 1..3), mid rows; rows without in-arcs only through d0_list
+    int32_t r_small, n_small, r_small4, n_small4, r_lane, n_lane, r_mid, n_mid;
+    int32_t r_d0;                              // first row without in-arcs
+    const int4 *__restrict__ lane_tab;         // aligned with [r_lane, r_lane + n_lane)
+    int32_t *d0_list;                          // rows without in-arcs whose state can
+                                               // change (listed at step 0), ctl->d0_n
     int32_t *cand_small;
     int32_t *cand_mid;
     uint32_t *bitmap;
     const int32_t *__restrict__ list_in;   // rows listed by the previous step
     int32_t *list_out;                     // rows listed for the next step
-    // hubs
-    const int32_t *__restrict__ hub_rows;
+    // hubs: new ids 0 .. n_hubs-1
     const int64_t *__restrict__ hub_chunk_base;
     int32_t n_hubs;
     int64_t n_hub_chunks;
@@ -111,6 +112,14 @@ struct StepArgs {
     uint32_t *hub_scratch;          // [n_hubs][Wn*32] per-lane counts (IC: [n_hubs][Wn] masks)
     unsigned long long *prof_bytes; // [FSGP_PROF_KINDS] algorithmic bytes per kind, or null
 };
+
+// Node (Philox subject) of new row i, and new row of node v.
+__device__ __forceinline__ uint32_t node_of(const StepArgs &A, int32_t i) {
+    return A.orig ? (uint32_t)__ldg(A.orig + i) : (uint32_t)i;
+}
+__device__ __forceinline__ int32_t row_of(const StepArgs &A, int32_t v) {
+    return A.pos ? __ldg(A.pos + v) : v;
+}
 
 // profile kinds (fsgp_profile)
 enum { PK_INIT = 0, PK_BEGIN = 1, PK_MARK = 2, PK_HUB = 3, PK_HUBFIN = 4, PK_MID = 5,
