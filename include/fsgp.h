@@ -128,7 +128,9 @@ typedef struct {
     fsgp_profile *profile;  /* optional host struct, accumulated (not cleared) */
     int32_t capture_graph;  /* 1: capture the step loop of each launch wave into a CUDA
                                graph and launch it at once (ignored when profiling) */
-    int32_t reserved[7];
+    int32_t lane_words;     /* words per thread of the one-thread-per-row kernel (rows with
+                               1..3 in-arcs): 1, 2, 4 or 8 (0 = auto) */
+    int32_t reserved[6];
 } fsgp_options;
 
 /* Caller-owned result buffers, all host or all device (flags).  NULL = not wanted,

@@ -384,8 +384,14 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
 
 // Hub rows, phase 1: one CTA per (chunk of in-arcs, word slice); per-lane partial counts
 // (IC: live masks) are added into the hub's scratch slot.
+//   pass 0: every chunk;
+//   pass 1 (SIR/SIS): the first chunk of every hub row only; when every susceptible lane
+//     of the slice already counts K_sat infected in-arcs there, the slice is flagged:
+//     its lanes are infected whatever the rest of the row holds (every count from K_sat
+//     on decides the same way), so its other chunks need not be read;
+//   pass 2 (SIR/SIS): the other chunks of the slices not flagged.
 template <int MODEL, int V, int TEAM>
-__global__ void __launch_bounds__(kBlock, min_ctas<V, true>()) k_hub_chunks(StepArgs A) {
+__global__ void __launch_bounds__(kBlock, min_ctas<V, true>()) k_hub_chunks(StepArgs A, int pass) {
     __shared__ uint32_t s_cnt[kMaxR];
     constexpr int B = kWideBits;
     constexpr int TPB = kBlock / TEAM;
@@ -400,16 +406,25 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, true>()) k_hub_chunks(Step
     const int lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < SW * 32; i += blockDim.x) s_cnt[i] = 0u;
     __syncthreads();
-    const int64_t n_items = A.n_hub_chunks * A.nslices;
+    const int64_t n_items = (pass == 1 ? (int64_t)A.n_hubs : A.n_hub_chunks) * A.nslices;
     for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const int64_t item = it / A.nslices;
+        int64_t item = it / A.nslices;      // chunk index (pass 1: hub index)
         const int slice = (int)(it - item * A.nslices);
-        int lo = 0, hi = A.n_hubs - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(A.hub_chunk_base + mid) <= item) lo = mid; else hi = mid - 1;
+        int h;
+        if (pass == 1) {
+            h = (int)item;
+            item = __ldg(A.hub_chunk_base + h);
+        } else {
+            int lo = 0, hi = A.n_hubs - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(A.hub_chunk_base + mid) <= item) lo = mid; else hi = mid - 1;
+            }
+            h = lo;
+            if (pass == 2 && (item == __ldg(A.hub_chunk_base + h) ||
+                              *(volatile const uint32_t *)&A.hub_sat[(int64_t)h * A.nslices + slice]))
+                continue;   // the first chunk ran in pass 1, or the slice is saturated
         }
-        const int h = lo;
         const int32_t v = h;   // hub rows are new ids 0 .. n_hubs-1
         if (sparse && !((A.bitmap[v >> 5] >> (v & 31)) & 1u)) continue;
         const int ws0 = slice * SW;        // first word of the slice
@@ -485,6 +500,28 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, true>()) k_hub_chunks(Step
         if (A.prof_bytes && threadIdx.x == 0)
             atomicAdd(&A.prof_bytes[PK_HUB], row_bytes(SW, P, true, end - beg));
         __syncthreads();
+        if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SIS) {
+            if (pass == 1) {
+                // team 0 holds the slice's susceptible lanes (need); all of them at K_sat?
+                bool sat = true;
+                if (team == 0) {
+#pragma unroll
+                    for (int i = 0; i < V; ++i) {
+                        const int32_t ks = __ldg(&A.sp[x[i].s].ksat);
+                        uint32_t m = need[i];
+                        if (m && ks == INT32_MAX) sat = false;
+                        const int wsl = w0 + i - ws0;
+                        while (m && sat) {
+                            const int l = __ffs(m) - 1;
+                            m &= m - 1;
+                            if (s_cnt[wsl * 32 + l] < (uint32_t)ks) sat = false;
+                        }
+                    }
+                }
+                if (__syncthreads_and(sat) && threadIdx.x == 0)
+                    A.hub_sat[(int64_t)h * A.nslices + slice] = 1u;
+            }
+        }
         uint32_t *slot = A.hub_scratch + (size_t)h * nl;
         if constexpr (ModelTraits<MODEL>::counts) {
             for (int i = threadIdx.x; i < SW * 32; i += blockDim.x) {
@@ -590,6 +627,8 @@ __global__ void __launch_bounds__(kBlock) k_hub_finalize(StepArgs A) {
         }
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+        if (A.hub_sat)
+            for (int sl = lane; sl < A.nslices; sl += 32) A.hub_sat[h * A.nslices + sl] = 0u;
         const bool want = cand && lane == 0 && fl != 0u;
         if (want && (fl & 1u)) acc.push_deg += (unsigned long long)(__ldg(A.out_ptr + node + 1) - __ldg(A.out_ptr + node));
         if (A.prof_bytes && cand && lane == 0)
@@ -837,7 +876,12 @@ int launch_rows_vt(const StepArgs &A, const StepLaunch &L, cudaStream_t s) {
     Prof *pr = L.prof;
     if (L.have_hub) {
         if (pr) pr->start(PK_HUB, s);
-        k_hub_chunks<MODEL, V, TEAM><<<L.grid_hub, kBlock, 0, s>>>(A);
+        if (A.hub_sat) {
+            k_hub_chunks<MODEL, V, TEAM><<<L.grid_hub, kBlock, 0, s>>>(A, 1);
+            k_hub_chunks<MODEL, V, TEAM><<<L.grid_hub, kBlock, 0, s>>>(A, 2);
+        } else {
+            k_hub_chunks<MODEL, V, TEAM><<<L.grid_hub, kBlock, 0, s>>>(A, 0);
+        }
         if (pr) { pr->stop(s); pr->start(PK_HUBFIN, s); }
         k_hub_finalize<MODEL><<<L.grid_fin, kBlock, L.smem_lanes, s>>>(A);
         if (pr) pr->stop(s);
@@ -915,7 +959,7 @@ int launch_rows(const StepArgs &A, const StepLaunch &L, cudaStream_t s) {
 // a split row.
 template <int MODEL, int V, int TEAM>
 int launch_split_vt(const StepArgs &A, int grid_chunks, int grid_fin, cudaStream_t s) {
-    k_hub_chunks<MODEL, V, TEAM><<<grid_chunks, kBlock, 0, s>>>(A);
+    k_hub_chunks<MODEL, V, TEAM><<<grid_chunks, kBlock, 0, s>>>(A, 0);
     k_hub_finalize<MODEL><<<grid_fin, kBlock, 0, s>>>(A);
     return FSGP_OK;
 }

@@ -443,6 +443,11 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     const int SW = std::min(32 * V, pd);
     const int TEAM = SW / V;
     const int nslices = Wn / SW;
+    // words per thread of the one-thread-per-row kernel
+    if (opt.lane_words != 0 && opt.lane_words != 1 && opt.lane_words != 2 && opt.lane_words != 4 &&
+        opt.lane_words != 8)
+        return fail(FSGP_EINVAL, "lane_words must be 1, 2, 4 or 8");
+    const int lane_swl = std::min(opt.lane_words > 0 ? opt.lane_words : 8, pd);
     const bool host_out = sets[0]->out_flags == FSGP_PTR_HOST;
     bool want_lanes = false, want_freq = false, any_init = false, want_steps = false;
     for (int i = 0; i < S; ++i) {
@@ -521,13 +526,13 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     const size_t state_words = (size_t)P * n * Wn;
     enum { O_STATE, O_PC, O_CTL, O_LIST0, O_LIST1, O_CSMALL, O_CMID, O_BITMAP, O_LANES,
            O_HUB, O_SURV, O_SEEDS, O_COUNTS, O_FREQ, O_PREAL, O_PLANES, O_PROF, O_SP, O_OUT,
-           O_STEPS, O_D0, O_END };
+           O_STEPS, O_D0, O_HUBSAT, O_END };
     size_t sz[O_END] = {0};
     sz[O_STATE] = 2 * state_words * sizeof(uint32_t);
     sz[O_PC] = T1 * S * 2 * sizeof(unsigned long long);
     sz[O_CTL] = sizeof(Ctl);
     // a row is listed once per work item: slices of the team kernels or of the lane kernel
-    sz[O_LIST0] = sz[O_LIST1] = (size_t)n * std::max(nslices, Wn / std::min(8, pd)) * sizeof(int32_t);
+    sz[O_LIST0] = sz[O_LIST1] = (size_t)n * std::max(nslices, Wn / lane_swl) * sizeof(int32_t);
     sz[O_CSMALL] = sz[O_CMID] = (size_t)n * sizeof(int32_t);
     sz[O_BITMAP] = ((size_t)n + 31) / 32 * sizeof(uint32_t);
     sz[O_LANES] = want_lanes ? 2 * (size_t)Wn * 32 * sizeof(int32_t) : 0;
@@ -543,6 +548,8 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     sz[O_OUT] = (size_t)S * sizeof(SetOut);
     sz[O_STEPS] = (size_t)S * sizeof(int32_t);
     sz[O_D0] = (size_t)n_d0 * sizeof(int32_t);
+    const bool hub_sat = model == FSGP_SIR || model == FSGP_SIS;
+    sz[O_HUBSAT] = hub_sat ? (size_t)n_hubs * nslices * sizeof(uint32_t) : 0;
     size_t off[O_END], total = 0;
     for (int i = 0; i < O_END; ++i) {
         off[i] = total;
@@ -589,7 +596,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     const size_t smem_lanes = want_lanes ? 2 * (size_t)Wn * 32 * sizeof(int32_t) : 0;
     if (smem_lanes > 32 * 1024) return fail(FSGP_EINVAL, "per-lane counters exceed shared memory");
     RowOccupancy occ{};
-    occ.swl = std::min(8, pd);   // words per thread of the one-thread-per-row kernel
+    occ.swl = lane_swl;
     rc = occupancy_model(model, V, TEAM, smem_lanes, &occ);
     if (rc) return rc;
     Prof prof;
@@ -668,6 +675,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     A.n_hub_chunks = g->hub.n_chunks;
     A.hub_chunk = chunk;
     A.hub_scratch = hub_scratch;
+    A.hub_sat = (hub_sat && n_hubs > 0) ? (uint32_t *)(ws + off[O_HUBSAT]) : nullptr;
     A.prof_bytes = profiling ? d_prof : nullptr;
 
     FSGP_CUDA(cudaMemsetAsync(ws + off[O_STATE], 0, sz[O_STATE], s));
@@ -681,6 +689,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     FSGP_CUDA(cudaMemsetAsync(A.bitmap, 0, sz[O_BITMAP], s));
     if (A.lane_cnt) FSGP_CUDA(cudaMemsetAsync(A.lane_cnt, 0, sz[O_LANES], s));
     if (sz[O_HUB]) FSGP_CUDA(cudaMemsetAsync(hub_scratch, 0, sz[O_HUB], s));
+    if (sz[O_HUBSAT]) FSGP_CUDA(cudaMemsetAsync(A.hub_sat, 0, sz[O_HUBSAT], s));
     if (profiling) {
         FSGP_CUDA(cudaMemsetAsync(d_prof, 0, sz[O_PROF], s));
         prof.start(PK_INIT, s);
@@ -751,7 +760,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
         }
         rc = launch_rows_model(model, A, L, s);
         if (rc) return rc;
-        launches += 1 + (allow_sparse ? 1 : 0) + (L.have_hub ? 2 : 0) + (L.have_mid ? 1 : 0) +
+        launches += 1 + (allow_sparse ? 1 : 0) + (L.have_hub ? (A.hub_sat ? 3 : 2) : 0) + (L.have_mid ? 1 : 0) +
                     (L.have_small ? 1 : 0) + (L.have_small4 ? 1 : 0) + (L.have_lane ? 1 : 0);
     }
     FSGP_CUDA(cudaGetLastError());

@@ -110,6 +110,8 @@ struct StepArgs {
     int64_t n_hub_chunks;
     int32_t hub_chunk;
     uint32_t *hub_scratch;          // [n_hubs][Wn*32] per-lane counts (IC: [n_hubs][Wn] masks)
+    uint32_t *hub_sat;              // SIR/SIS: [n_hubs][nslices] the slice's susceptible lanes
+                                    // all reached K_sat within the row's first chunk, or null
     unsigned long long *prof_bytes; // [FSGP_PROF_KINDS] algorithmic bytes per kind, or null
 };
 
