@@ -1,4 +1,4 @@
-"""CPU oracle for batched Monte Carlo propagation (SIR, SIS, IC, LT).
+"""CPU oracle for batched Monte Carlo propagation (SIR, SIS, IC, LT, SI, SEIR, SEIS, SWIR).
 
 TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` are the only callers.  The product path never imports
@@ -29,7 +29,8 @@ _lock = threading.Lock()
 _lib = None
 
 SIR, SIS, IC, LT = 0, 1, 2, 3
-TAG_INFECT, TAG_RECOVER, TAG_IC_EDGE, TAG_LT_THRESH = 1, 2, 3, 4
+SI, SEIR, SEIS, SWIR = 4, 5, 6, 7
+TAG_INFECT, TAG_RECOVER, TAG_IC_EDGE, TAG_LT_THRESH, TAG_LATENT, TAG_WEAKEN = 1, 2, 3, 4, 5, 6
 IC_WEIGHTED_CASCADE, IC_CONSTANT = 0, 1
 
 
@@ -67,6 +68,15 @@ def _load():
                 ctypes.c_uint64, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                 ctypes.c_int, P, P, P, P, P]
             lib.orc_simulate.restype = ctypes.c_int
+            lib.orc_simulate_ext.argtypes = [
+                ctypes.c_int, ctypes.c_int32, P, P, ctypes.c_double, ctypes.c_double,
+                ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                P, ctypes.c_int64, ctypes.c_int32,
+                ctypes.c_uint64, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                ctypes.c_int, P, P, P, P, P]
+            lib.orc_simulate_ext.restype = ctypes.c_int
+            lib.orc_compartments.argtypes = [ctypes.c_int]
+            lib.orc_compartments.restype = ctypes.c_int
             lib.orc_node_step.argtypes = [
                 ctypes.c_int, P, P, ctypes.c_int32, P, ctypes.c_double, ctypes.c_double,
                 ctypes.c_int, ctypes.c_double, ctypes.c_uint32, ctypes.c_uint32,
@@ -105,21 +115,27 @@ def prob_threshold(p: float) -> int:
     return int(_load().orc_prob_threshold(float(p)))
 
 
+def compartments(model: int) -> int:
+    """Compartments reported for a model: 4 for SEIR and SWIR, 3 otherwise."""
+    return int(_load().orc_compartments(int(model)))
+
+
 @dataclass
 class OracleResult:
-    counts: np.ndarray        # [T+1, 3] u64 over the realizations run
-    per_real: np.ndarray      # [n_real, T+1, 3] u32
-    freq: np.ndarray          # [3, n] u32
+    counts: np.ndarray        # [T+1, C] u64 over the realizations run
+    per_real: np.ndarray      # [n_real, T+1, C] u32
+    freq: np.ndarray          # [C, n] u32
     final_state: np.ndarray   # [n_real, n] u8 (0/1/2)
     quiet_step: np.ndarray    # [n_real] i32 (IC/LT: first step with empty frontier)
 
 
 def simulate(model: int, row_ptr, col_idx, seeds, *, beta=0.0, gamma=0.0,
-             ic_mode=IC_WEIGHTED_CASCADE, ic_p=0.0, R=1, T=0, rng_seed=0,
-             r_lo=0, n_real=None, init_state=None, t0=0, nthreads=None,
+             ic_mode=IC_WEIGHTED_CASCADE, ic_p=0.0, alpha=0.0, mu=0.0, nu=0.0, R=1, T=0,
+             rng_seed=0, r_lo=0, n_real=None, init_state=None, t0=0, nthreads=None,
              outputs=("counts", "per_real", "freq", "final_state")) -> OracleResult:
     """Run realizations r_lo .. r_lo+n_real-1 of one seed set on the in-CSR graph.
-    `outputs` limits which result arrays are produced (counts always are)."""
+    `outputs` limits which result arrays are produced (counts always are).  alpha is the
+    SEIR/SEIS latent rate (E -> I); SWIR takes kappa = beta, mu and nu."""
     lib = _load()
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
     col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
@@ -129,19 +145,21 @@ def simulate(model: int, row_ptr, col_idx, seeds, *, beta=0.0, gamma=0.0,
         n_real = R - r_lo
     if nthreads is None:
         nthreads = os.cpu_count() or 1
-    counts = np.zeros((T + 1, 3), dtype=np.uint64)
-    per_real = np.zeros((n_real, T + 1, 3), dtype=np.uint32) if "per_real" in outputs else None
-    freq = np.zeros((3, n), dtype=np.uint32) if "freq" in outputs else None
+    C = compartments(model)
+    counts = np.zeros((T + 1, C), dtype=np.uint64)
+    per_real = np.zeros((n_real, T + 1, C), dtype=np.uint32) if "per_real" in outputs else None
+    freq = np.zeros((C, n), dtype=np.uint32) if "freq" in outputs else None
     final_state = np.zeros((n_real, n), dtype=np.uint8) if "final_state" in outputs else None
     quiet = np.zeros(n_real, dtype=np.int32)
     if init_state is not None:
         init_state = np.ascontiguousarray(init_state, dtype=np.uint8)
         assert init_state.shape == (n_real, n)
-    rc = lib.orc_simulate(int(model), n, _ptr(row_ptr), _ptr(col_idx), float(beta),
-                          float(gamma), int(ic_mode), float(ic_p), _ptr(seeds),
-                          int(seeds.shape[0]), int(T), int(rng_seed), _ptr(init_state),
-                          int(t0), int(r_lo), int(n_real), int(nthreads), _ptr(counts),
-                          _ptr(per_real), _ptr(freq), _ptr(final_state), _ptr(quiet))
+    rc = lib.orc_simulate_ext(int(model), n, _ptr(row_ptr), _ptr(col_idx), float(beta),
+                              float(gamma), int(ic_mode), float(ic_p), float(alpha), float(mu),
+                              float(nu), _ptr(seeds), int(seeds.shape[0]), int(T), int(rng_seed),
+                              _ptr(init_state), int(t0), int(r_lo), int(n_real), int(nthreads),
+                              _ptr(counts), _ptr(per_real), _ptr(freq), _ptr(final_state),
+                              _ptr(quiet))
     if rc != 0:
         raise ValueError(f"orc_simulate failed with code {rc}")
     return OracleResult(counts, per_real, freq, final_state, quiet)

@@ -29,6 +29,16 @@
  *  - LT (named in Sec. 1; definition taken from the project statement): per node and
  *    realization threshold theta = u(tag 4, v, t=0, r); an inactive node with k >= 1
  *    active in-arcs activates iff k*2^32 >= theta*d_in(v).
+ *  - The discrete-time epidemic rows of Table 1 (named there, rules not written out;
+ *    k counts the in-arcs whose source is infectious, I):
+ *      SI: SIR without recovery (I absorbing).
+ *      SEIR(DT): S -> E iff k >= 1 and u >= surv_beta[k]; E -> I iff u(tag 5) <
+ *        llrint(alpha*2^32); I -> R iff u(tag 2) < llrint(gamma*2^32).
+ *      SEIS(DT): the same with I -> S.
+ *      SWIR: S -> I iff k >= 1 and u >= surv_kappa[k] (kappa = beta), otherwise
+ *        S -> W iff k >= 1 and u(tag 6) >= surv_mu[k]; W -> I iff k >= 1 and u >=
+ *        surv_nu[k]; I -> R at the next step.
+ *    Every node changes state at most once per step, from its step-(t-1) state.
  *
  * Uniforms (bit-plane contract): P_j = Philox4x32_10(key=(lo32(seed),hi32(seed)),
  * ctr=(a, t, r>>5, (tag<<8)|(j>>2)))[j&3] for j = 0..31, and bit (31-j) of u is bit
@@ -44,17 +54,37 @@
 #define ORC_SIS 1
 #define ORC_IC 2
 #define ORC_LT 3
+#define ORC_SI 4
+#define ORC_SEIR 5
+#define ORC_SEIS 6
+#define ORC_SWIR 7
 
 #define TAG_INFECT 1u
 #define TAG_RECOVER 2u
 #define TAG_IC_EDGE 3u
 #define TAG_LT_THRESH 4u
+#define TAG_LATENT 5u
+#define TAG_WEAKEN 6u
 
-/* node states.  SIR/SIS: 0=S 1=I 2=R.  IC/LT: 0=inactive 1=newly active (frontier)
- * 2=active since an earlier step. */
+/* node states (= compartment index).  SIR/SIS: 0=S 1=I 2=R.  IC/LT: 0=inactive 1=newly
+ * active (frontier) 2=active since an earlier step.  SI: 0=S 1=I.  SEIR/SEIS: 0=S 1=E
+ * 2=I 3=R.  SWIR: 0=S 1=W 2=I 3=R. */
 #define ST_0 0
 #define ST_1 1
 #define ST_2 2
+#define ST_3 3
+
+/* compartments reported per model (columns of counts / rows of freq) */
+int orc_compartments(int model)
+{
+    return (model == ORC_SEIR || model == ORC_SWIR) ? 4 : 3;
+}
+
+/* state that transmits (counted in k) and the state seeds start in */
+static uint8_t infectious_state(int model)
+{
+    return (model == ORC_SEIR || model == ORC_SEIS || model == ORC_SWIR) ? ST_2 : ST_1;
+}
 
 /* ---------------- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) --------------
  * One round: two 32x32->64 multiplies of counter words 0 and 2 by the round
@@ -134,6 +164,8 @@ typedef struct {
     int64_t n_seeds;
     int32_t T;
     uint64_t rng_seed;
+    double alpha, mu, nu;     /* SEIR/SEIS latent rate; SWIR weakening and weakened infection */
+    int C;                    /* compartments */
     const uint8_t *init_state; /* optional [n_real][n] start states (resume); NULL = seeds */
     int32_t t0;               /* absolute index of the starting step */
     int32_t r_lo, n_real;     /* realizations r_lo .. r_lo+n_real-1 */
@@ -145,9 +177,12 @@ typedef struct {
     int32_t *quiet_step;  /* [n_real]: IC/LT first step with an empty frontier (T if never) */
     /* derived */
     uint64_t *surv;
+    uint64_t *surv_mu;    /* SWIR */
+    uint64_t *surv_nu;    /* SWIR */
     int64_t kmax;
     uint64_t g_rec;
     uint64_t p_const;
+    uint64_t a_lat;       /* SEIR/SEIS latent threshold */
 } orc_job;
 
 typedef struct {
@@ -206,15 +241,62 @@ static uint8_t node_update(const orc_job *jb, const uint8_t *X, int32_t v, uint3
         if (((uint64_t)k << 32) >= (uint64_t)theta * (uint64_t)d) return ST_1;
         return ST_0;
     }
+    case ORC_SI: {
+        if (s != ST_0) return s;
+        int64_t k = 0;
+        for (int32_t e = beg; e < end; ++e)
+            if (X[jb->col_idx[e]] == ST_1) ++k;
+        if (k == 0) return ST_0;
+        uint32_t u = orc_uniform(jb->rng_seed, TAG_INFECT, (uint32_t)v, t, r);
+        return ((uint64_t)u >= jb->surv[k <= jb->kmax ? k : jb->kmax]) ? ST_1 : ST_0;
+    }
+    case ORC_SEIR:
+    case ORC_SEIS: {
+        if (s == ST_0) {
+            int64_t k = 0;
+            for (int32_t e = beg; e < end; ++e)
+                if (X[jb->col_idx[e]] == ST_2) ++k;
+            if (k == 0) return ST_0;
+            uint32_t u = orc_uniform(jb->rng_seed, TAG_INFECT, (uint32_t)v, t, r);
+            return ((uint64_t)u >= jb->surv[k <= jb->kmax ? k : jb->kmax]) ? ST_1 : ST_0;
+        }
+        if (s == ST_1) {
+            uint32_t u = orc_uniform(jb->rng_seed, TAG_LATENT, (uint32_t)v, t, r);
+            return ((uint64_t)u < jb->a_lat) ? ST_2 : ST_1;
+        }
+        if (s == ST_2) {
+            uint32_t u = orc_uniform(jb->rng_seed, TAG_RECOVER, (uint32_t)v, t, r);
+            if ((uint64_t)u < jb->g_rec) return jb->model == ORC_SEIR ? ST_3 : ST_0;
+            return ST_2;
+        }
+        return ST_3;
+    }
+    case ORC_SWIR: {
+        if (s == ST_0 || s == ST_1) {
+            int64_t k = 0;
+            for (int32_t e = beg; e < end; ++e)
+                if (X[jb->col_idx[e]] == ST_2) ++k;
+            if (k == 0) return s;
+            const int64_t kk = k <= jb->kmax ? k : jb->kmax;
+            uint32_t u = orc_uniform(jb->rng_seed, TAG_INFECT, (uint32_t)v, t, r);
+            if (s == ST_0) {
+                if ((uint64_t)u >= jb->surv[kk]) return ST_2;
+                uint32_t w = orc_uniform(jb->rng_seed, TAG_WEAKEN, (uint32_t)v, t, r);
+                return ((uint64_t)w >= jb->surv_mu[kk]) ? ST_1 : ST_0;
+            }
+            return ((uint64_t)u >= jb->surv_nu[kk]) ? ST_2 : ST_1;
+        }
+        return ST_3;   /* I -> R after one step; R absorbing */
+    }
     }
     return s;
 }
 
-static void tally(const orc_job *jb, const uint8_t *X, uint64_t *cnt3)
+static void tally(const orc_job *jb, const uint8_t *X, uint64_t *cnt)
 {
-    uint64_t c[3] = {0, 0, 0};
+    uint64_t c[4] = {0, 0, 0, 0};
     for (int32_t v = 0; v < jb->n; ++v) c[X[v]]++;
-    cnt3[0] += c[0]; cnt3[1] += c[1]; cnt3[2] += c[2];
+    for (int i = 0; i < jb->C; ++i) cnt[i] += c[i];
 }
 
 static void *worker_main(void *arg)
@@ -227,17 +309,18 @@ static void *worker_main(void *arg)
     for (int32_t ri = w->tid; ri < jb->n_real; ri += w->nthreads) {
         const uint32_t r = (uint32_t)(jb->r_lo + ri);
         /* X^0 */
+        const int C = jb->C;
         if (jb->init_state) {
             memcpy(X, jb->init_state + (size_t)ri * n, (size_t)n);
         } else {
             memset(X, ST_0, (size_t)n);
-            for (int64_t i = 0; i < jb->n_seeds; ++i) X[jb->seeds[i]] = ST_1;
+            for (int64_t i = 0; i < jb->n_seeds; ++i) X[jb->seeds[i]] = infectious_state(jb->model);
         }
-        uint64_t c0[3] = {0, 0, 0};
+        uint64_t c0[4] = {0, 0, 0, 0};
         tally(jb, X, c0);
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < C; ++c) {
             w->counts[c] += c0[c];
-            if (jb->per_real) jb->per_real[((size_t)ri * (T + 1)) * 3 + c] = (uint32_t)c0[c];
+            if (jb->per_real) jb->per_real[((size_t)ri * (T + 1)) * C + c] = (uint32_t)c0[c];
         }
         int quiet = 0;
         int32_t quiet_step = T;
@@ -257,11 +340,11 @@ static void *worker_main(void *arg)
                     if (!any_front) { quiet = 1; quiet_step = k; }
                 }
             }
-            uint64_t ck[3] = {0, 0, 0};
+            uint64_t ck[4] = {0, 0, 0, 0};
             tally(jb, X, ck);
-            for (int c = 0; c < 3; ++c) {
-                w->counts[(size_t)k * 3 + c] += ck[c];
-                if (jb->per_real) jb->per_real[((size_t)ri * (T + 1) + k) * 3 + c] = (uint32_t)ck[c];
+            for (int c = 0; c < C; ++c) {
+                w->counts[(size_t)k * C + c] += ck[c];
+                if (jb->per_real) jb->per_real[((size_t)ri * (T + 1) + k) * C + c] = (uint32_t)ck[c];
             }
         }
         if (jb->quiet_step) jb->quiet_step[ri] = quiet_step;
@@ -277,19 +360,20 @@ static void *worker_main(void *arg)
 /*
  * Run n_real realizations (r_lo .. r_lo+n_real-1) of one model from one seed set.
  * Returns 0 on success, -1 on invalid arguments, -2 on allocation failure.
- * counts must hold (T+1)*3 u64, per_real (optional) n_real*(T+1)*3 u32,
- * freq (optional) 3*n u32, final_state (optional) n_real*n u8, quiet_step
- * (optional) n_real i32.
+ * With C = orc_compartments(model): counts must hold (T+1)*C u64, per_real (optional)
+ * n_real*(T+1)*C u32, freq (optional) C*n u32, final_state (optional) n_real*n u8,
+ * quiet_step (optional) n_real i32.
  */
-int orc_simulate(int model, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
-                 double beta, double gamma, int ic_mode, double ic_p,
-                 const int32_t *seeds, int64_t n_seeds, int32_t T, uint64_t rng_seed,
-                 const uint8_t *init_state, int32_t t0,
-                 int32_t r_lo, int32_t n_real, int nthreads,
-                 uint64_t *counts, uint32_t *per_real, uint32_t *freq, uint8_t *final_state,
-                 int32_t *quiet_step)
+int orc_simulate_ext(int model, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                     double beta, double gamma, int ic_mode, double ic_p,
+                     double alpha, double mu, double nu,
+                     const int32_t *seeds, int64_t n_seeds, int32_t T, uint64_t rng_seed,
+                     const uint8_t *init_state, int32_t t0,
+                     int32_t r_lo, int32_t n_real, int nthreads,
+                     uint64_t *counts, uint32_t *per_real, uint32_t *freq, uint8_t *final_state,
+                     int32_t *quiet_step)
 {
-    if (model < 0 || model > 3 || n < 0 || T < 0 || n_real < 0 || r_lo < 0 || !counts) return -1;
+    if (model < 0 || model > 7 || n < 0 || T < 0 || n_real < 0 || r_lo < 0 || !counts) return -1;
     if (nthreads < 1) nthreads = 1;
     for (int64_t i = 0; i < n_seeds; ++i)
         if (seeds[i] < 0 || seeds[i] >= n) return -1;
@@ -297,6 +381,7 @@ int orc_simulate(int model, int32_t n, const int32_t *row_ptr, const int32_t *co
     memset(&jb, 0, sizeof jb);
     jb.model = model; jb.n = n; jb.row_ptr = row_ptr; jb.col_idx = col_idx;
     jb.beta = beta; jb.gamma = gamma; jb.ic_mode = ic_mode; jb.ic_p = ic_p;
+    jb.alpha = alpha; jb.mu = mu; jb.nu = nu; jb.C = orc_compartments(model);
     jb.seeds = seeds; jb.n_seeds = n_seeds; jb.T = T; jb.rng_seed = rng_seed;
     jb.init_state = init_state; jb.t0 = t0;
     jb.r_lo = r_lo; jb.n_real = n_real;
@@ -309,35 +394,59 @@ int orc_simulate(int model, int32_t n, const int32_t *row_ptr, const int32_t *co
     }
     jb.kmax = maxdeg;
     jb.surv = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(maxdeg + 1));
-    if (!jb.surv) return -2;
+    jb.surv_mu = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(maxdeg + 1));
+    jb.surv_nu = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(maxdeg + 1));
+    if (!jb.surv || !jb.surv_mu || !jb.surv_nu) {
+        free(jb.surv); free(jb.surv_mu); free(jb.surv_nu);
+        return -2;
+    }
     orc_survival_table(beta, maxdeg, jb.surv);
+    orc_survival_table(mu, maxdeg, jb.surv_mu);
+    orc_survival_table(nu, maxdeg, jb.surv_nu);
     jb.g_rec = orc_prob_threshold(gamma);
     jb.p_const = orc_prob_threshold(ic_p);
+    jb.a_lat = orc_prob_threshold(alpha);
+    const int C = jb.C;
 
-    memset(counts, 0, sizeof(uint64_t) * (size_t)(T + 1) * 3);
-    if (freq) memset(freq, 0, sizeof(uint32_t) * 3 * (size_t)n);
+    memset(counts, 0, sizeof(uint64_t) * (size_t)(T + 1) * C);
+    if (freq) memset(freq, 0, sizeof(uint32_t) * C * (size_t)n);
     if (nthreads > n_real && n_real > 0) nthreads = n_real;
     orc_worker *ws = (orc_worker *)calloc((size_t)nthreads, sizeof(orc_worker));
     pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
     int rc = 0;
     for (int i = 0; i < nthreads; ++i) {
         ws[i].job = &jb; ws[i].tid = i; ws[i].nthreads = nthreads;
-        ws[i].counts = (uint64_t *)calloc((size_t)(T + 1) * 3, sizeof(uint64_t));
-        ws[i].freq = freq ? (uint32_t *)calloc(3 * (size_t)n + 1, sizeof(uint32_t)) : NULL;
+        ws[i].counts = (uint64_t *)calloc((size_t)(T + 1) * C, sizeof(uint64_t));
+        ws[i].freq = freq ? (uint32_t *)calloc((size_t)C * n + 1, sizeof(uint32_t)) : NULL;
         if (!ws[i].counts || (freq && !ws[i].freq)) rc = -2;
     }
     if (rc == 0) {
         for (int i = 0; i < nthreads; ++i) pthread_create(&th[i], NULL, worker_main, &ws[i]);
         for (int i = 0; i < nthreads; ++i) pthread_join(th[i], NULL);
         for (int i = 0; i < nthreads; ++i) {
-            for (size_t j = 0; j < (size_t)(T + 1) * 3; ++j) counts[j] += ws[i].counts[j];
+            for (size_t j = 0; j < (size_t)(T + 1) * C; ++j) counts[j] += ws[i].counts[j];
             if (freq)
-                for (size_t j = 0; j < 3 * (size_t)n; ++j) freq[j] += ws[i].freq[j];
+                for (size_t j = 0; j < (size_t)C * n; ++j) freq[j] += ws[i].freq[j];
         }
     }
     for (int i = 0; i < nthreads; ++i) { free(ws[i].counts); free(ws[i].freq); }
-    free(ws); free(th); free(jb.surv);
+    free(ws); free(th); free(jb.surv); free(jb.surv_mu); free(jb.surv_nu);
     return rc;
+}
+
+/* The four models of the first table rows (SIR, SIS, IC, LT): three compartments. */
+int orc_simulate(int model, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                 double beta, double gamma, int ic_mode, double ic_p,
+                 const int32_t *seeds, int64_t n_seeds, int32_t T, uint64_t rng_seed,
+                 const uint8_t *init_state, int32_t t0,
+                 int32_t r_lo, int32_t n_real, int nthreads,
+                 uint64_t *counts, uint32_t *per_real, uint32_t *freq, uint8_t *final_state,
+                 int32_t *quiet_step)
+{
+    if (model < 0 || model > 3) return -1;
+    return orc_simulate_ext(model, n, row_ptr, col_idx, beta, gamma, ic_mode, ic_p, 0.0, 0.0, 0.0,
+                            seeds, n_seeds, T, rng_seed, init_state, t0, r_lo, n_real, nthreads,
+                            counts, per_real, freq, final_state, quiet_step);
 }
 
 /* Step-by-step single-node check used for sampled parity at full size: the state of
@@ -358,7 +467,8 @@ int orc_node_step(int model, const int32_t *row_ptr, const int32_t *col_idx, int
     orc_survival_table(beta, d, jb.surv);
     jb.g_rec = orc_prob_threshold(gamma);
     jb.p_const = orc_prob_threshold(ic_p);
-    int s = node_update(&jb, X, v, t, r);
+    jb.C = orc_compartments(model);
+    int s = (model >= 0 && model <= 3) ? node_update(&jb, X, v, t, r) : -1;
     free(jb.surv);
     return s;
 }

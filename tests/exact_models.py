@@ -155,3 +155,72 @@ def chi_square_gof(observed: dict, expected_prob: dict, n_samples: int, alpha=1e
     stat = float(((obs - exp) ** 2 / exp).sum())
     df = max(1, len(obs) - 1)
     return stat, float(stats.chi2.ppf(1 - alpha, df)), df
+
+
+def chain_state_distribution(row_ptr, col_idx, init, T, transitions, n_states):
+    """Exact distribution of the compartment counts after T synchronous steps of a model
+    whose per-node transition depends only on the node's state and on k, the number of
+    its in-arcs (with multiplicity) whose source is infectious.  transitions(state, k)
+    returns [(new_state, probability), ...]; init is the tuple of start states; the
+    infectious state is given by transitions.infectious."""
+    n = len(row_ptr) - 1
+    in_nb = [[int(col_idx[e]) for e in range(row_ptr[v], row_ptr[v + 1])] for v in range(n)]
+    inf = transitions.infectious
+    cur = {tuple(init): 1.0}
+    for _ in range(T):
+        nxt = defaultdict(float)
+        for st, p in cur.items():
+            opts = []
+            for v in range(n):
+                k = sum(1 for u in in_nb[v] if st[u] == inf)
+                opts.append([o for o in transitions(st[v], k) if o[1] > 0.0])
+            for combo in itertools.product(*opts):
+                q = p
+                for (_, w) in combo:
+                    q *= w
+                if q > 0.0:
+                    nxt[tuple(s for (s, _) in combo)] += q
+        cur = nxt
+    out = defaultdict(float)
+    for st, p in cur.items():
+        out[tuple(st.count(c) for c in range(n_states))] += p
+    return dict(out)
+
+
+class SeirRule:
+    """SEIR / SEIS (discrete time): S -> E with 1-(1-beta)^k, E -> I with alpha, I -> R
+    (SEIS: S) with gamma.  States 0 S, 1 E, 2 I, 3 R."""
+    infectious = 2
+
+    def __init__(self, beta, alpha, gamma, sis=False):
+        self.b, self.a, self.g, self.sis = beta, alpha, gamma, sis
+
+    def __call__(self, s, k):
+        if s == 0:
+            p = 1.0 - (1.0 - self.b) ** k if k > 0 else 0.0
+            return [(1, p), (0, 1.0 - p)]
+        if s == 1:
+            return [(2, self.a), (1, 1.0 - self.a)]
+        if s == 2:
+            return [(0 if self.sis else 3, self.g), (2, 1.0 - self.g)]
+        return [(3, 1.0)]
+
+
+class SwirRule:
+    """SWIR: S -> I with 1-(1-kappa)^k, else S -> W with 1-(1-mu)^k; W -> I with
+    1-(1-nu)^k; I -> R after one step.  States 0 S, 1 W, 2 I, 3 R."""
+    infectious = 2
+
+    def __init__(self, kappa, mu, nu):
+        self.k, self.m, self.n = kappa, mu, nu
+
+    def __call__(self, s, k):
+        def p_of(x):
+            return 1.0 - (1.0 - x) ** k if k > 0 else 0.0
+        if s == 0:
+            pi, pw = p_of(self.k), p_of(self.m)
+            return [(2, pi), (1, (1.0 - pi) * pw), (0, (1.0 - pi) * (1.0 - pw))]
+        if s == 1:
+            pi = p_of(self.n)
+            return [(2, pi), (1, 1.0 - pi)]
+        return [(3, 1.0)]
