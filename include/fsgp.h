@@ -65,10 +65,24 @@ extern "C" {
 #define FSGP_SIS 1   /* planes: 0 = I */
 #define FSGP_IC 2    /* planes: 0 = A (active), 1 = F (activated at the last step) */
 #define FSGP_LT 3    /* planes: 0 = A, 1 = F */
+/* The discrete-time epidemic rows of Table 1 (named there; the rules are this library's
+ * reading, k = in-arcs whose source is infectious, counted with multiplicity):
+ *   SI: SIR without recovery.
+ *   SEIR(DT): S -> E iff u >= surv_beta[k]; E -> I iff u(tag 5) < llrint(alpha * 2^32);
+ *     I -> R iff u(tag 2) < llrint(gamma * 2^32).  SEIS(DT): the same with I -> S.
+ *   SWIR: S -> I iff u >= surv_kappa[k] (kappa = beta), else S -> W iff u(tag 6) >=
+ *     surv_mu[k]; W -> I iff u >= surv_nu[k]; I -> R after one step.
+ *   One change per node, lane and step, from the state of the previous step. */
+#define FSGP_SI 4    /* planes: 0 = I */
+#define FSGP_SEIR 5  /* planes: 0 = I, 1 = R, 2 = E (exposed) */
+#define FSGP_SEIS 6  /* planes: 0 = I, 1 = E */
+#define FSGP_SWIR 7  /* planes: 0 = I, 1 = R, 2 = W (weakened) */
 
-/* Compartments reported in counts / freq / per-realization counts, index 0,1,2:
- *   SIR: S, I, R.  SIS: S, I, 0.  IC and LT: inactive, newly active (F), active
- *   before the last step (A and not F). */
+/* Compartments reported in counts / freq / per-realization counts (C per model, see
+ * fsgp_model_compartments), in this order:
+ *   SIR: S, I, R.  SIS and SI: S, I, 0.  IC and LT: inactive, newly active (F), active
+ *   before the last step (A and not F).  SEIR: S, E, I, R.  SEIS: S, E, I.
+ *   SWIR: S, W, I, R. */
 
 /* ------------------------------------------------------------------------- flags */
 #define FSGP_PTR_HOST 0u
@@ -82,10 +96,13 @@ extern "C" {
 typedef struct fsgp_graph fsgp_graph;
 
 typedef struct {
-    double beta;      /* SIR/SIS per-arc infection probability, [0, 1] */
-    double gamma;     /* SIR/SIS recovery probability, [0, 1] */
+    double beta;      /* per-arc infection probability (SWIR: kappa), [0, 1] */
+    double gamma;     /* recovery probability, [0, 1] */
     int32_t ic_mode;  /* FSGP_IC_WEIGHTED_CASCADE or FSGP_IC_CONSTANT */
     double ic_p;      /* IC constant arc probability, [0, 1] */
+    double alpha;     /* SEIR/SEIS: exposed -> infectious probability per step, [0, 1] */
+    double mu;        /* SWIR: per-arc weakening probability, [0, 1] */
+    double nu;        /* SWIR: per-arc infection probability of a weakened node, [0, 1] */
 } fsgp_params;
 
 /* Optional per-kernel profile of one fsgp_simulate call (host struct).  Device times
@@ -137,9 +154,9 @@ typedef struct {
  * except counts.  W = ceil(R / 32). */
 typedef struct {
     uint32_t flags;          /* FSGP_PTR_HOST or FSGP_PTR_DEVICE */
-    uint64_t *counts;        /* [n_sets][T+1][3]: compartment totals over all lanes */
-    uint32_t *freq;          /* [n_sets][3][n]: per-node final compartment frequency */
-    uint32_t *per_real;      /* [n_sets][R][T+1][3]: per-realization compartment counts */
+    uint64_t *counts;        /* [n_sets][T+1][C]: compartment totals over all lanes */
+    uint32_t *freq;          /* [n_sets][C][n]: per-node final compartment frequency */
+    uint32_t *per_real;      /* [n_sets][R][T+1][C]: per-realization compartment counts */
     uint32_t *final_planes;  /* [n_sets][planes][n][W]: final state bit-planes */
     int32_t *steps_run;      /* [n_sets]: transitions computed (IC/LT stop at the first
                                 step that activates nothing; later rows repeat) */
@@ -171,8 +188,12 @@ int fsgp_graph_trim(fsgp_graph *g);
 int fsgp_graph_info(const fsgp_graph *g, int32_t *n, int64_t *nnz, int32_t *max_in_degree,
                     int64_t *device_bytes);
 
-/* Number of state bit-planes of a model (2 for SIR, IC, LT; 1 for SIS), or EINVAL. */
+/* Number of state bit-planes of a model (1 for SIS and SI; 2 for SIR, IC, LT, SEIS;
+ * 3 for SEIR and SWIR), or EINVAL. */
 int fsgp_model_planes(int32_t model);
+
+/* Number of compartments C a model reports (4 for SEIR and SWIR, 3 otherwise), or EINVAL. */
+int fsgp_model_compartments(int32_t model);
 
 /* Run R realizations of `model` for T synchronous steps from each of n_sets seed sets
  * (paper API: run_epochs(epochs = R, times = T), Sec. 4.2.1).

@@ -49,8 +49,11 @@ int probe(fsgp_graph *g, int model, const fsgp_params *p, const int32_t *seeds, 
           float *ms) {
     SetSpec x{};
     x.beta = p->beta;
-    x.gamma = p->gamma;
+    x.gamma = model == FSGP_SI ? 0.0 : p->gamma;
     x.ic_p = p->ic_p;
+    x.alpha = p->alpha;
+    x.mu = p->mu;
+    x.nu = p->nu;
     x.rng_seed = rng_seed;
     x.R = R;
     x.seeds = seeds;
@@ -62,7 +65,7 @@ int probe(fsgp_graph *g, int model, const fsgp_params *p, const int32_t *seeds, 
     FSGP_CUDA(cudaEventCreate(&a));
     FSGP_CUDA(cudaEventCreate(&b));
     cudaEventRecord(a, s);
-    int rc = run_sets(g, model, p->ic_mode, &x, 1, T, opt, s);
+    int rc = run_sets(g, model == FSGP_SI ? FSGP_SIS : model, p->ic_mode, &x, 1, T, opt, s);
     cudaEventRecord(b, s);
     cudaError_t e = cudaEventSynchronize(b);
     if (rc == FSGP_OK && e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
@@ -84,7 +87,7 @@ extern "C" int fsgp_autotune(const fsgp_graph *gc, int32_t model, const fsgp_par
     set_error("");
     fsgp_graph *g = const_cast<fsgp_graph *>(gc);
     if (!g || !params || !inout || (n_seeds > 0 && !seed_nodes)) return fail(FSGP_EINVAL, "NULL argument");
-    if (model < FSGP_SIR || model > FSGP_LT) return fail(FSGP_EINVAL, "unknown model");
+    if (model < FSGP_SIR || model > FSGP_SWIR) return fail(FSGP_EINVAL, "unknown model");
     if (R < 1 || R > kMaxR) return fail(FSGP_EINVAL, "R must be in [1, 4096]");
     if (T_probe < 1) return fail(FSGP_EINVAL, "T_probe must be >= 1");
     cudaStream_t s = (cudaStream_t)stream;
@@ -142,7 +145,7 @@ extern "C" int fsgp_batch_run(const fsgp_request *reqs, int32_t n, const fsgp_ba
         const fsgp_request &q = reqs[i];
         if (!q.graph) return fail(FSGP_EINVAL, "request without a graph");
         if (q.graph->device != dev) return fail(FSGP_EINVAL, "request graph on another device");
-        if (q.model < FSGP_SIR || q.model > FSGP_LT) return fail(FSGP_EINVAL, "unknown model");
+        if (q.model < FSGP_SIR || q.model > FSGP_SWIR) return fail(FSGP_EINVAL, "unknown model");
         if (q.R < 1 || q.R > kMaxR) return fail(FSGP_EINVAL, "R must be in [1, 4096]");
         if (q.T < 0) return fail(FSGP_EINVAL, "T must be >= 0");
         if (q.n_seeds < 0 || (q.n_seeds > 0 && !q.seed_nodes)) return fail(FSGP_EINVAL, "bad seed set");
@@ -160,7 +163,8 @@ extern "C" int fsgp_batch_run(const fsgp_request *reqs, int32_t n, const fsgp_ba
     std::map<const fsgp_graph *, double> cost;
     for (int i = 0; i < n; ++i) {
         const fsgp_request &q = reqs[i];
-        groups[Key(q.graph, q.model, q.params.ic_mode, q.T)].push_back(i);
+        // SI runs as SIS without recovery
+        groups[Key(q.graph, q.model == FSGP_SI ? FSGP_SIS : q.model, q.params.ic_mode, q.T)].push_back(i);
         cost[q.graph] += (double)(q.graph->nnz + q.graph->n) * q.R * std::max(q.T, 1);
     }
     // per-graph tuning (optional): one probe series on the graph's first request
@@ -229,8 +233,11 @@ extern "C" int fsgp_batch_run(const fsgp_request *reqs, int32_t n, const fsgp_ba
                     SetSpec &x = specs[j];
                     x = SetSpec{};
                     x.beta = q.params.beta;
-                    x.gamma = q.params.gamma;
+                    x.gamma = q.model == FSGP_SI ? 0.0 : q.params.gamma;
                     x.ic_p = q.params.ic_p;
+                    x.alpha = q.params.alpha;
+                    x.mu = q.params.mu;
+                    x.nu = q.params.nu;
                     x.rng_seed = q.rng_seed;
                     x.R = q.R;
                     x.seeds = q.seed_nodes;

@@ -17,6 +17,8 @@ constexpr uint32_t TAG_INFECT = 1u;
 constexpr uint32_t TAG_RECOVER = 2u;
 constexpr uint32_t TAG_IC_EDGE = 3u;
 constexpr uint32_t TAG_LT_THRESH = 4u;
+constexpr uint32_t TAG_LATENT = 5u;
+constexpr uint32_t TAG_WEAKEN = 6u;
 constexpr uint64_t TWO32 = 4294967296ull;
 
 constexpr int kBlock = 256;          // threads per CTA for the row kernels

@@ -322,8 +322,17 @@ extern "C" int fsgp_model_planes(int32_t model) {
         case FSGP_SIS: return 1;
         case FSGP_IC: return 2;
         case FSGP_LT: return 2;
+        case FSGP_SI: return 1;
+        case FSGP_SEIR: return 3;
+        case FSGP_SEIS: return 2;
+        case FSGP_SWIR: return 3;
         default: return fail(FSGP_EINVAL, "unknown model");
     }
+}
+
+extern "C" int fsgp_model_compartments(int32_t model) {
+    if (model < FSGP_SIR || model > FSGP_SWIR) return fail(FSGP_EINVAL, "unknown model");
+    return (model == FSGP_SEIR || model == FSGP_SWIR) ? 4 : 3;
 }
 
 extern "C" int fsgp_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t n,

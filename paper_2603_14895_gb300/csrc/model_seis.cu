@@ -1,0 +1,9 @@
+// model_seis.cu -- row kernels of the SEIS model (one translation unit per model so that the
+// template instantiations compile in parallel).
+#include "rows.cuh"
+
+namespace fsgp {
+template int launch_rows<FSGP_SEIS>(const StepArgs &, const StepLaunch &, cudaStream_t);
+template int occupancy_rows<FSGP_SEIS>(int, int, size_t, RowOccupancy *);
+template int launch_split_rows<FSGP_SEIS>(const StepArgs &, int, int, int, int, cudaStream_t);
+}  // namespace fsgp

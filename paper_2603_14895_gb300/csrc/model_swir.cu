@@ -1,0 +1,9 @@
+// model_swir.cu -- row kernels of the SWIR model (one translation unit per model so that the
+// template instantiations compile in parallel).
+#include "rows.cuh"
+
+namespace fsgp {
+template int launch_rows<FSGP_SWIR>(const StepArgs &, const StepLaunch &, cudaStream_t);
+template int occupancy_rows<FSGP_SWIR>(int, int, size_t, RowOccupancy *);
+template int launch_split_rows<FSGP_SWIR>(const StepArgs &, int, int, int, int, cudaStream_t);
+}  // namespace fsgp

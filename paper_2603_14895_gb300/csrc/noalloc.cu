@@ -35,7 +35,7 @@ constexpr size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Fixed head of the scratch (byte offsets).
 constexpr size_t kOffCtl = 0;
-constexpr size_t kOffPc = 256;            // 2 x u64 plane popcounts
+constexpr size_t kOffPc = 256;            // kPC x u64 plane popcounts (2 used)
 constexpr size_t kOffInfo = 512;          // u64 info[4]: max in-degree, chunks, k_sat
 constexpr size_t kOffSet = 768;           // SetParams of the single set
 constexpr size_t kOffSurv = 1024;         // (kSurvCap + 1) x u64
@@ -165,6 +165,8 @@ extern "C" int fsgp_step_noalloc(int32_t model, const fsgp_params *params, const
                                  uint32_t t, uint64_t rng_seed, const uint32_t *cur_planes,
                                  uint32_t *next_planes, uint64_t *plane_counts, void *stream) {
     set_error("");
+    if (model > FSGP_LT && model <= FSGP_SWIR)
+        return fail(FSGP_EUNSUPPORTED, "this entry point covers the SIR, SIS, IC and LT models");
     if (model < FSGP_SIR || model > FSGP_LT) return fail(FSGP_EINVAL, "unknown model");
     if (!params || !row_ptr || !cur_planes || !next_planes || !plane_counts || (nnz > 0 && !col_idx))
         return fail(FSGP_EINVAL, "NULL argument");

@@ -40,11 +40,62 @@ __device__ __forceinline__ void st_vec(uint32_t *p, const uint32_t (&w)[V]) {
 
 template <int MODEL>
 struct ModelTraits {
-    static constexpr int planes = MODEL == FSGP_SIS ? 1 : 2;
-    // plane gathered from in-neighbours: I (SIR/SIS), F (IC), A (LT)
+    // SIR: I, R.  SIS: I.  IC, LT: A, F.  SEIR: I, R, E.  SEIS: I, E.  SWIR: I, R, W.
+    static constexpr int planes = MODEL == FSGP_SIS ? 1 : ((MODEL == FSGP_SEIR || MODEL == FSGP_SWIR) ? 3 : 2);
+    // plane gathered from in-neighbours: I (epidemic models), F (IC), A (LT)
     static constexpr int src_plane = MODEL == FSGP_IC ? 1 : 0;
     static constexpr bool counts = MODEL != FSGP_IC;
+    // the state's source lanes are plane 1 (F) for IC / LT, plane 0 (I) otherwise
+    static constexpr bool cascade = MODEL == FSGP_IC || MODEL == FSGP_LT;
+    // hub rows may stop reading once every susceptible lane reaches K_sat
+    static constexpr bool saturates = MODEL == FSGP_SIR || MODEL == FSGP_SIS || MODEL == FSGP_SEIR ||
+                                      MODEL == FSGP_SEIS;
 };
+
+// Lanes that can change through their in-arcs: susceptible (SWIR: also weakened) or
+// inactive lanes.
+template <int MODEL>
+__device__ __forceinline__ uint32_t need_of(uint32_t vm, uint32_t s0, uint32_t s1, uint32_t s2) {
+    if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SEIS || MODEL == FSGP_SWIR) return vm & ~s0 & ~s1;
+    else if constexpr (MODEL == FSGP_SEIR) return vm & ~s0 & ~s1 & ~s2;
+    else return vm & ~s0;
+}
+
+// One word of the synchronous update (Eq. updata) from the in-arc counts c (IC: the
+// lanes made active by a live arc, `newly`).
+template <int MODEL, int B>
+__device__ __forceinline__ WordOut update_word(const StepArgs &A, uint32_t node, const WordCtx &x, uint32_t s0,
+                                               uint32_t s1, uint32_t s2, int32_t d, const uint32_t (&c)[B],
+                                               uint32_t newly) {
+    WordOut o;
+    if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SIS) {
+        o = update_sir_word<MODEL, B>(A, node, x, s0, s1, d, c);
+    } else if constexpr (MODEL == FSGP_IC) {
+        o.n0 = s0 | newly;
+        o.n1 = newly;
+        o.n2 = 0u;
+    } else if constexpr (MODEL == FSGP_LT) {
+        o = update_lt_word<B>(A, node, x, s0, d, c);
+    } else if constexpr (MODEL == FSGP_SWIR) {
+        o = update_swir_word<B>(A, node, x, s0, s1, s2, d, c);
+    } else {
+        o = update_seir_word<MODEL, B>(A, node, x, s0, s1, s2, d, c);
+    }
+    return o;
+}
+
+// Row flags of a decided word: bit 0 the new state has source lanes (its out-neighbours
+// are pressed next step), bit 1 the row changed or can change on its own next step
+// (an exposed lane: SEIR / SEIS).
+template <int MODEL>
+__device__ __forceinline__ uint32_t word_flags(const WordOut &o, uint32_t s0, uint32_t s1, uint32_t s2) {
+    uint32_t fl = 0u;
+    if (o.n0 != s0 || o.n1 != s1 || o.n2 != s2) fl |= 2u;
+    if (ModelTraits<MODEL>::cascade ? (o.n1 != 0u) : (o.n0 != 0u)) fl |= 1u;
+    if constexpr (MODEL == FSGP_SEIR) if (o.n2) fl |= 2u;
+    if constexpr (MODEL == FSGP_SEIS) if (o.n1) fl |= 2u;
+    return fl;
+}
 
 // IC live-arc threshold of a word: weighted cascade (live iff u * d < 2^32, i.e.
 // u < floor((2^32 - 1) / d) + 1) or the set's constant probability.
@@ -128,7 +179,7 @@ constexpr int min_ctas() { return V == 4 ? 2 : (V == 2 ? (WIDE ? 3 : 4) : 4); }
 template <int MODEL, int V, int TEAM, bool WARP_ROW, int BT = kSmallBits>
 __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepArgs A, int which) {
     extern __shared__ int32_t s_lane[];
-    __shared__ unsigned long long s_pc[2 * kMaxSets];
+    __shared__ unsigned long long s_pc[kPC * kMaxSets];
     constexpr int B = WARP_ROW ? kWideBits : BT;
     constexpr int TPW = 32 / TEAM;
     constexpr int SW = TEAM * V;
@@ -152,7 +203,7 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
     const bool lanes_on = A.lane_cnt != nullptr;
     const bool build = list_wanted(A);
     if (lanes_on)
-        for (int i = threadIdx.x; i < 2 * nl; i += blockDim.x) s_lane[i] = 0;
+        for (int i = threadIdx.x; i < A.np * nl; i += blockDim.x) s_lane[i] = 0;
     set_acc_zero(s_pc, A.S);
     const int lane = threadIdx.x & 31;
     const int team = lane / TEAM;
@@ -168,9 +219,9 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
     // when a row is a single slice).
     int ctx_slice = -1;
     WordCtx x[V];
-    int32_t d0[V], d1[V];
+    int32_t d0[V], d1[V], d2[V];
 #pragma unroll
-    for (int i = 0; i < V; ++i) d0[i] = d1[i] = 0;
+    for (int i = 0; i < V; ++i) d0[i] = d1[i] = d2[i] = 0;
 
     for (int64_t base = gwarp * RPI; base < nitems; base += nwarps * RPI) {
         const int64_t item = WARP_ROW ? base : base + team;
@@ -184,8 +235,8 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
         if (slice != ctx_slice) {
 #pragma unroll
             for (int i = 0; i < V; ++i) {
-                if (ctx_slice >= 0) set_acc_add(s_pc, x[i].s, d0[i], d1[i]);
-                d0[i] = d1[i] = 0;
+                if (ctx_slice >= 0) set_acc_add(s_pc, x[i].s, d0[i], d1[i], d2[i]);
+                d0[i] = d1[i] = d2[i] = 0;
                 x[i] = word_ctx(A, w0 + i);
             }
             ctx_slice = slice;
@@ -194,12 +245,13 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
         uint32_t need[V];
         {
             Vec<V> a = has_row ? ldg_vec<V>(A.cur + off) : Vec<V>{};
-            Vec<V> b{};
-            if (MODEL == FSGP_SIR && has_row) b = ldg_vec<V>(A.cur + A.plane_words + off);
+            Vec<V> b{}, e{};
+            if (P >= 2 && MODEL != FSGP_IC && MODEL != FSGP_LT && has_row) b = ldg_vec<V>(A.cur + A.plane_words + off);
+            if (MODEL == FSGP_SEIR && has_row) e = ldg_vec<V>(A.cur + 2 * A.plane_words + off);
 #pragma unroll
             for (int i = 0; i < V; ++i) {
                 const uint32_t vm = has_row ? x[i].vm : 0u;
-                need[i] = MODEL == FSGP_SIR ? (vm & ~a.w[i] & ~b.w[i]) : (vm & ~a.w[i]);
+                need[i] = need_of<MODEL>(vm, a.w[i], b.w[i], e.w[i]);
             }
         }
         uint32_t any_need = 0u;
@@ -293,31 +345,26 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
                     }
                 }
                 const uint32_t s0 = __ldg(A.cur + off + i);
-                const uint32_t s1 = P == 2 ? __ldg(A.cur + A.plane_words + off + i) : 0u;
-                WordOut o;
-                if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SIS) {
-                    o = update_sir_word<MODEL, B>(A, node, xw, s0, s1, end - beg, cw);
-                } else if constexpr (MODEL == FSGP_IC) {
-                    o.n0 = s0 | nw;
-                    o.n1 = nw;
-                } else {
-                    o = update_lt_word<B>(A, node, xw, s0, end - beg, cw);
-                }
+                const uint32_t s1 = P >= 2 ? __ldg(A.cur + A.plane_words + off + i) : 0u;
+                const uint32_t s2 = P >= 3 ? __ldg(A.cur + 2 * A.plane_words + off + i) : 0u;
+                const WordOut o = update_word<MODEL, B>(A, node, xw, s0, s1, s2, end - beg, cw, nw);
                 A.nxt[off + i] = o.n0;
-                if (P == 2) A.nxt[A.plane_words + off + i] = o.n1;
+                if (P >= 2) A.nxt[A.plane_words + off + i] = o.n1;
+                if (P >= 3) A.nxt[2 * A.plane_words + off + i] = o.n2;
 #pragma unroll
                 for (int q = 0; q < V; ++q) {
                     if (i == q) {
                         d0[q] += __popc(o.n0) - __popc(s0);
                         d1[q] += __popc(o.n1) - __popc(s1);
+                        d2[q] += __popc(o.n2) - __popc(s2);
                     }
                 }
                 if (lanes_on) {
                     lane_deltas(s_lane, w0 + i, s0, o.n0);
-                    if (P == 2) lane_deltas(s_lane + nl, w0 + i, s1, o.n1);
+                    if (P >= 2) lane_deltas(s_lane + nl, w0 + i, s1, o.n1);
+                    if (P >= 3) lane_deltas(s_lane + 2 * nl, w0 + i, s2, o.n2);
                 }
-                if (o.n0 != s0 || o.n1 != s1) fl |= 2u;
-                if ((MODEL == FSGP_SIR || MODEL == FSGP_SIS) ? (o.n0 != 0u) : (o.n1 != 0u)) fl |= 1u;
+                fl |= word_flags<MODEL>(o, s0, s1, s2);
             }
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) fl |= __shfl_xor_sync(0xffffffffu, fl, o);
@@ -326,42 +373,39 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
         writer = has_row && (!WARP_ROW || team == 0);
         if (writer) {
             // own state again (L1/L2-resident): not kept live across the gather
-            uint32_t s0[V], s1[V];
+            uint32_t s0[V], s1[V], s2[V];
             {
                 Vec<V> a = ldg_vec<V>(A.cur + off);
-                Vec<V> b{};
-                if (P == 2) b = ldg_vec<V>(A.cur + A.plane_words + off);
+                Vec<V> b{}, e{};
+                if (P >= 2) b = ldg_vec<V>(A.cur + A.plane_words + off);
+                if (P >= 3) e = ldg_vec<V>(A.cur + 2 * A.plane_words + off);
 #pragma unroll
                 for (int i = 0; i < V; ++i) {
                     s0[i] = a.w[i];
-                    s1[i] = P == 2 ? b.w[i] : 0u;
+                    s1[i] = P >= 2 ? b.w[i] : 0u;
+                    s2[i] = P >= 3 ? e.w[i] : 0u;
                 }
             }
-            uint32_t n0[V], n1[V];
+            uint32_t n0[V], n1[V], n2[V];
 #pragma unroll
             for (int i = 0; i < V; ++i) {
-                WordOut o;
-                if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SIS) {
-                    o = update_sir_word<MODEL, B>(A, node, x[i], s0[i], s1[i], end - beg, c[i]);
-                } else if constexpr (MODEL == FSGP_IC) {
-                    o.n0 = s0[i] | newly[i];
-                    o.n1 = newly[i];
-                } else {
-                    o = update_lt_word<B>(A, node, x[i], s0[i], end - beg, c[i]);
-                }
+                const WordOut o = update_word<MODEL, B>(A, node, x[i], s0[i], s1[i], s2[i], end - beg, c[i], newly[i]);
                 n0[i] = o.n0;
                 n1[i] = o.n1;
+                n2[i] = o.n2;
                 d0[i] += __popc(o.n0) - __popc(s0[i]);
                 d1[i] += __popc(o.n1) - __popc(s1[i]);
+                d2[i] += __popc(o.n2) - __popc(s2[i]);
                 if (lanes_on) {
                     lane_deltas(s_lane, w0 + i, s0[i], o.n0);
-                    if (P == 2) lane_deltas(s_lane + nl, w0 + i, s1[i], o.n1);
+                    if (P >= 2) lane_deltas(s_lane + nl, w0 + i, s1[i], o.n1);
+                    if (P >= 3) lane_deltas(s_lane + 2 * nl, w0 + i, s2[i], o.n2);
                 }
-                if (o.n0 != s0[i] || o.n1 != s1[i]) fl |= 2u;
-                if ((MODEL == FSGP_SIR || MODEL == FSGP_SIS) ? (o.n0 != 0u) : (o.n1 != 0u)) fl |= 1u;
+                fl |= word_flags<MODEL>(o, s0[i], s1[i], s2[i]);
             }
             st_vec<V>(A.nxt + off, n0);
-            if (P == 2) st_vec<V>(A.nxt + A.plane_words + off, n1);
+            if (P >= 2) st_vec<V>(A.nxt + A.plane_words + off, n1);
+            if (P >= 3) st_vec<V>(A.nxt + 2 * A.plane_words + off, n2);
         }
 #pragma unroll
         for (int o = 1; o < TEAM; o <<= 1) fl |= __shfl_xor_sync(0xffffffffu, fl, o);
@@ -375,7 +419,7 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
     }
     if (ctx_slice >= 0) {
 #pragma unroll
-        for (int i = 0; i < V; ++i) set_acc_add(s_pc, x[i].s, d0[i], d1[i]);
+        for (int i = 0; i < V; ++i) set_acc_add(s_pc, x[i].s, d0[i], d1[i], d2[i]);
     }
     flush_accum(A, acc, list_slot, WARP_ROW ? PK_MID : (BT == 4 ? PK_SMALL4 : PK_SMALL));
     set_acc_flush(A, s_pc);
@@ -435,12 +479,13 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, true>()) k_hub_chunks(Step
         {
             const size_t off = (size_t)v * A.Wn + w0;
             Vec<V> a = ldg_vec<V>(A.cur + off);
-            Vec<V> b{};
-            if (P == 2) b = ldg_vec<V>(A.cur + A.plane_words + off);
+            Vec<V> b{}, e{};
+            if (P >= 2) b = ldg_vec<V>(A.cur + A.plane_words + off);
+            if (P >= 3) e = ldg_vec<V>(A.cur + 2 * A.plane_words + off);
 #pragma unroll
             for (int i = 0; i < V; ++i) {
                 x[i] = word_ctx(A, w0 + i);
-                need[i] = MODEL == FSGP_SIR ? (x[i].vm & ~a.w[i] & ~b.w[i]) : (x[i].vm & ~a.w[i]);
+                need[i] = need_of<MODEL>(x[i].vm, a.w[i], b.w[i], e.w[i]);
                 any_need |= need[i];
             }
         }
@@ -500,7 +545,7 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, true>()) k_hub_chunks(Step
         if (A.prof_bytes && threadIdx.x == 0)
             atomicAdd(&A.prof_bytes[PK_HUB], row_bytes(SW, P, true, end - beg));
         __syncthreads();
-        if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SIS) {
+        if constexpr (ModelTraits<MODEL>::saturates) {
             if (pass == 1) {
                 // team 0 holds the slice's susceptible lanes (need); all of them at K_sat?
                 bool sat = true;
@@ -549,7 +594,7 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, true>()) k_hub_chunks(Step
 template <int MODEL>
 __global__ void __launch_bounds__(kBlock) k_hub_finalize(StepArgs A) {
     extern __shared__ int32_t s_lane[];
-    __shared__ unsigned long long s_pc[2 * kMaxSets];
+    __shared__ unsigned long long s_pc[kPC * kMaxSets];
     constexpr int P = ModelTraits<MODEL>::planes;
     const Ctl *C = A.ctl;
     if (*(volatile const int32_t *)&C->stop) return;
@@ -558,7 +603,7 @@ __global__ void __launch_bounds__(kBlock) k_hub_finalize(StepArgs A) {
     const bool lanes_on = A.lane_cnt != nullptr;
     const bool build = list_wanted(A);
     if (lanes_on)
-        for (int i = threadIdx.x; i < 2 * nl; i += blockDim.x) s_lane[i] = 0;
+        for (int i = threadIdx.x; i < A.np * nl; i += blockDim.x) s_lane[i] = 0;
     set_acc_zero(s_pc, A.S);
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -600,28 +645,21 @@ __global__ void __launch_bounds__(kBlock) k_hub_finalize(StepArgs A) {
                 if (act) {
                     const size_t off = (size_t)v * A.Wn + w;
                     const uint32_t s0 = __ldg(A.cur + off);
-                    const uint32_t s1 = P == 2 ? __ldg(A.cur + A.plane_words + off) : 0u;
+                    const uint32_t s1 = P >= 2 ? __ldg(A.cur + A.plane_words + off) : 0u;
+                    const uint32_t s2 = P >= 3 ? __ldg(A.cur + 2 * A.plane_words + off) : 0u;
                     const WordCtx x = word_ctx(A, w);
-                    WordOut o;
-                    if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SIS) {
-                        o = update_sir_word<MODEL, 32>(A, node, x, s0, s1, d, c);
-                    } else if constexpr (MODEL == FSGP_IC) {
-                        const uint32_t nw2 = newly & x.vm & ~s0;
-                        o.n0 = s0 | nw2;
-                        o.n1 = nw2;
-                    } else {
-                        o = update_lt_word<32>(A, node, x, s0, d, c);
-                    }
+                    const WordOut o = update_word<MODEL, 32>(A, node, x, s0, s1, s2, d, c, newly & x.vm & ~s0);
                     A.nxt[off] = o.n0;
-                    if (P == 2) A.nxt[A.plane_words + off] = o.n1;
+                    if (P >= 2) A.nxt[A.plane_words + off] = o.n1;
+                    if (P >= 3) A.nxt[2 * A.plane_words + off] = o.n2;
                     set_acc_add(s_pc, x.s, (long long)__popc(o.n0) - __popc(s0),
-                                (long long)__popc(o.n1) - __popc(s1));
+                                (long long)__popc(o.n1) - __popc(s1), (long long)__popc(o.n2) - __popc(s2));
                     if (lanes_on) {
                         lane_deltas(s_lane, w, s0, o.n0);
-                        if (P == 2) lane_deltas(s_lane + nl, w, s1, o.n1);
+                        if (P >= 2) lane_deltas(s_lane + nl, w, s1, o.n1);
+                        if (P >= 3) lane_deltas(s_lane + 2 * nl, w, s2, o.n2);
                     }
-                    if (o.n0 != s0 || o.n1 != s1) fl |= 2u;
-                    if ((MODEL == FSGP_SIR || MODEL == FSGP_SIS) ? (o.n0 != 0u) : (o.n1 != 0u)) fl |= 1u;
+                    fl |= word_flags<MODEL>(o, s0, s1, s2);
                 }
             }
         }
@@ -653,17 +691,27 @@ __global__ void __launch_bounds__(kBlock) k_hub_finalize(StepArgs A) {
 // and then decides its words one at a time through a single, non-unrolled copy of the
 // per-word update (counts of at most 3 need 2-bit counters).
 constexpr int kLaneMaxDeg = 3;
-template <int SWL>
+template <int SWL, int NP>
 struct LaneStage {
-    uint32_t v[5][SWL][kBlock];   // own planes 0/1, then the sources' words (x0, x1, x2)
+    uint32_t v[NP + 3][SWL][kBlock];   // own planes, then the sources' words (x0, x1, x2)
 };
+
+// Lanes that change on their own (without in-arcs): infectious lanes that may recover,
+// newly active lanes that stop being new (IC / LT), exposed lanes (SEIR / SEIS).
+template <int MODEL>
+__device__ __forceinline__ uint32_t self_lanes(uint32_t s0, uint32_t s1, uint32_t s2) {
+    if constexpr (MODEL == FSGP_IC || MODEL == FSGP_LT) return s1;
+    else if constexpr (MODEL == FSGP_SEIR) return s0 | s2;
+    else if constexpr (MODEL == FSGP_SEIS) return s0 | s1;
+    else return s0;
+}
 
 template <int MODEL, int SWL>
 __global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
     extern __shared__ int32_t s_lane[];
-    __shared__ unsigned long long s_pc[2 * kMaxSets];
-    __shared__ LaneStage<SWL> st;
+    __shared__ unsigned long long s_pc[kPC * kMaxSets];
     constexpr int P = ModelTraits<MODEL>::planes;
+    __shared__ LaneStage<SWL, P> st;
     const Ctl *C = A.ctl;
     if (*(volatile const int32_t *)&C->stop) return;
     if (*(volatile const int32_t *)&C->sparse) return;
@@ -675,14 +723,14 @@ __global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
     const bool lanes_on = A.lane_cnt != nullptr;
     const bool build = list_wanted(A);
     if (lanes_on)
-        for (int i = threadIdx.x; i < 2 * nl; i += blockDim.x) s_lane[i] = 0;
+        for (int i = threadIdx.x; i < A.np * nl; i += blockDim.x) s_lane[i] = 0;
     set_acc_zero(s_pc, A.S);
     const int list_slot = A.k & 1;
     const int tid = threadIdx.x;
     const uint32_t *src_plane = A.cur + (size_t)ModelTraits<MODEL>::src_plane * A.plane_words;
     Accum acc;
     int cur_s = -1;           // set of the plane-count deltas not yet flushed
-    int32_t dd0 = 0, dd1 = 0;
+    int32_t dd0 = 0, dd1 = 0, dd2 = 0;
     for (int64_t item = (int64_t)blockIdx.x * blockDim.x + tid; item - tid < nitems;
          item += (int64_t)gridDim.x * blockDim.x) {
         const bool has = item < nitems;
@@ -713,13 +761,15 @@ __global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
             for (int q = 0; q < SWL; q += (SWL < 4 ? SWL : 4)) {
                 constexpr int VL = SWL < 4 ? SWL : 4;
                 const Vec<VL> a = ldg_vec<VL>(A.cur + off + q);
-                Vec<VL> bb{};
-                if (P == 2) bb = ldg_vec<VL>(A.cur + A.plane_words + off + q);
+                Vec<VL> bb{}, ee{};
+                if (P >= 2) bb = ldg_vec<VL>(A.cur + A.plane_words + off + q);
+                if (P >= 3) ee = ldg_vec<VL>(A.cur + 2 * A.plane_words + off + q);
                 uint32_t xs[VL];
 #pragma unroll
                 for (int i = 0; i < VL; ++i) {
                     st.v[0][q + i][tid] = a.w[i];
-                    st.v[1][q + i][tid] = P == 2 ? bb.w[i] : 0u;
+                    if (P >= 2) st.v[1][q + i][tid] = bb.w[i];
+                    if (P >= 3) st.v[2][q + i][tid] = ee.w[i];
                     xs[i] = 0u;
                 }
 #pragma unroll
@@ -728,15 +778,15 @@ __global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
                     if (u[j] >= 0) x = ldg_vec<VL>(src_plane + (size_t)u[j] * A.Wn + w0 + q);
 #pragma unroll
                     for (int i = 0; i < VL; ++i) {
-                        st.v[2 + j][q + i][tid] = x.w[i];
+                        st.v[P + j][q + i][tid] = x.w[i];
                         xs[i] |= x.w[i];
                     }
                 }
 #pragma unroll
                 for (int i = 0; i < VL; ++i) {
-                    const uint32_t s0 = a.w[i], s1 = P == 2 ? bb.w[i] : 0u;
-                    if (MODEL == FSGP_SIR || MODEL == FSGP_SIS) busy |= s0 | (~s0 & ~s1 & xs[i]);
-                    else busy |= s1 | (~s0 & xs[i]);   // IC/LT: the F plane clears, or lanes activate
+                    const uint32_t s0 = a.w[i], s1 = P >= 2 ? bb.w[i] : 0u, s2 = P >= 3 ? ee.w[i] : 0u;
+                    // a lane changes on its own, or can change with a set source lane
+                    busy |= self_lanes<MODEL>(s0, s1, s2) | (need_of<MODEL>(~0u, s0, s1, s2) & xs[i]);
                 }
             }
         }
@@ -747,79 +797,67 @@ __global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
 #pragma unroll
             for (int q = 0; q < SWL; q += (SWL < 4 ? SWL : 4)) {
                 constexpr int VL = SWL < 4 ? SWL : 4;
-                uint32_t n0[VL], n1[VL];
 #pragma unroll
-                for (int i = 0; i < VL; ++i) {
-                    n0[i] = st.v[0][q + i][tid];
-                    n1[i] = st.v[1][q + i][tid];
+                for (int pl = 0; pl < P; ++pl) {
+                    uint32_t nw[VL];
+#pragma unroll
+                    for (int i = 0; i < VL; ++i) nw[i] = st.v[pl][q + i][tid];
+                    st_vec<VL>(A.nxt + pl * A.plane_words + off + q, nw);
                 }
-                st_vec<VL>(A.nxt + off + q, n0);
-                if (P == 2) st_vec<VL>(A.nxt + A.plane_words + off + q, n1);
             }
         } else if (has) {
 #pragma unroll 1
             for (int i = 0; i < SWL; ++i) {
                 const WordCtx x = word_ctx(A, w0 + i);
-                const uint32_t s0 = st.v[0][i][tid], s1 = st.v[1][i][tid];
-                const uint32_t x0 = st.v[2][i][tid], x1 = st.v[3][i][tid], x2 = st.v[4][i][tid];
-                WordOut o;
+                const uint32_t s0 = st.v[0][i][tid];
+                const uint32_t s1 = P >= 2 ? st.v[1][i][tid] : 0u;
+                const uint32_t s2 = P >= 3 ? st.v[2][i][tid] : 0u;
+                const uint32_t x0 = st.v[P][i][tid], x1 = st.v[P + 1][i][tid], x2 = st.v[P + 2][i][tid];
+                const uint32_t need = need_of<MODEL>(x.vm, s0, s1, s2);
+                uint32_t c[2] = {0u, 0u}, newly = 0u;
                 if constexpr (MODEL == FSGP_IC) {
-                    const uint32_t need = x.vm & ~s0;
                     const uint64_t thr = ic_threshold(A, x.s, d);
-                    uint32_t newly = 0u;
                     const uint32_t xs[kLaneMaxDeg] = {x0, x1, x2};
 #pragma unroll
                     for (int j = 0; j < kLaneMaxDeg; ++j) {
                         const uint32_t m = xs[j] & need & ~newly;
                         if (m) newly |= lanes_u_less(m, thr, (uint32_t)(beg + j), A.t, x.g, TAG_IC_EDGE, x.k0, x.k1);
                     }
-                    o.n0 = s0 | newly;
-                    o.n1 = newly;
                 } else {
                     // counts of set source lanes (at most 3): two bit-planes
-                    uint32_t c[2];
-                    c[0] = x0 ^ x1 ^ x2;
-                    c[1] = (x0 & x1) | (x2 & (x0 ^ x1));
-                    if constexpr (MODEL == FSGP_LT) {
-                        const uint32_t need = x.vm & ~s0;
-                        c[0] &= need;
-                        c[1] &= need;
-                        o = update_lt_word<2>(A, node, x, s0, d, c);
-                    } else {
-                        const uint32_t need = x.vm & ~s0 & ~s1;
-                        c[0] &= need;
-                        c[1] &= need;
-                        o = update_sir_word<MODEL, 2>(A, node, x, s0, s1, d, c);
-                    }
+                    c[0] = (x0 ^ x1 ^ x2) & need;
+                    c[1] = ((x0 & x1) | (x2 & (x0 ^ x1))) & need;
                 }
+                const WordOut o = update_word<MODEL, 2>(A, node, x, s0, s1, s2, d, c, newly);
                 st.v[0][i][tid] = o.n0;
-                st.v[1][i][tid] = o.n1;
+                if (P >= 2) st.v[1][i][tid] = o.n1;
+                if (P >= 3) st.v[2][i][tid] = o.n2;
                 if (x.s != cur_s) {
-                    if (cur_s >= 0) set_acc_add(s_pc, cur_s, dd0, dd1);
+                    if (cur_s >= 0) set_acc_add(s_pc, cur_s, dd0, dd1, dd2);
                     cur_s = x.s;
-                    dd0 = dd1 = 0;
+                    dd0 = dd1 = dd2 = 0;
                 }
                 dd0 += __popc(o.n0) - __popc(s0);
                 dd1 += __popc(o.n1) - __popc(s1);
+                dd2 += __popc(o.n2) - __popc(s2);
                 if (lanes_on) {
                     lane_deltas(s_lane, w0 + i, s0, o.n0);
-                    if (P == 2) lane_deltas(s_lane + nl, w0 + i, s1, o.n1);
+                    if (P >= 2) lane_deltas(s_lane + nl, w0 + i, s1, o.n1);
+                    if (P >= 3) lane_deltas(s_lane + 2 * nl, w0 + i, s2, o.n2);
                 }
-                if (o.n0 != s0 || o.n1 != s1) fl |= 2u;
-                if ((MODEL == FSGP_SIR || MODEL == FSGP_SIS) ? (o.n0 != 0u) : (o.n1 != 0u)) fl |= 1u;
+                fl |= word_flags<MODEL>(o, s0, s1, s2);
             }
             const size_t off = (size_t)v * A.Wn + w0;
 #pragma unroll
             for (int q = 0; q < SWL; q += (SWL < 4 ? SWL : 4)) {
                 constexpr int VL = SWL < 4 ? SWL : 4;
-                uint32_t n0[VL], n1[VL];
 #pragma unroll
-                for (int i = 0; i < VL; ++i) {
-                    n0[i] = st.v[0][q + i][tid];
-                    n1[i] = st.v[1][q + i][tid];
+                for (int pl = 0; pl < P; ++pl) {
+                    uint32_t nw[VL];
+#pragma unroll
+                    for (int i = 0; i < VL; ++i) nw[i] = st.v[pl][q + i][tid];
+                    st_vec<VL>(A.nxt + pl * A.plane_words + off + q, nw);
                 }
-                st_vec<VL>(A.nxt + off + q, n0);
-                if (P == 2) st_vec<VL>(A.nxt + A.plane_words + off + q, n1);
             }
         }
         const bool want = has && fl != 0u;
@@ -827,11 +865,16 @@ __global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
         if (A.prof_bytes && has) acc.bytes += row_bytes(SWL, P, d > 0, d);
         list_append(A, build, want, (int32_t)((uint32_t)v | ((fl & 1u) ? kPushBit : 0u)), list_slot);
     }
-    if (cur_s >= 0) set_acc_add(s_pc, cur_s, dd0, dd1);
+    if (cur_s >= 0) set_acc_add(s_pc, cur_s, dd0, dd1, dd2);
     flush_accum(A, acc, list_slot, PK_LANE);
     set_acc_flush(A, s_pc);
     if (lanes_on) flush_lanes(A, s_lane, nl);
 }
+
+// Widest slice of the one-thread-per-row kernel: its staging area (planes + 3 sources,
+// SWL words, 256 threads) must fit the 48 KB of static shared memory.
+template <int MODEL>
+constexpr int lane_swl_max() { return ModelTraits<MODEL>::planes >= 3 ? 4 : 8; }
 
 template <int MODEL>
 int launch_rows_lane(const StepArgs &A, int swl, int grid, size_t smem, cudaStream_t s) {
@@ -839,7 +882,12 @@ int launch_rows_lane(const StepArgs &A, int swl, int grid, size_t smem, cudaStre
         case 1: k_rows_lane<MODEL, 1><<<grid, kBlock, smem, s>>>(A); break;
         case 2: k_rows_lane<MODEL, 2><<<grid, kBlock, smem, s>>>(A); break;
         case 4: k_rows_lane<MODEL, 4><<<grid, kBlock, smem, s>>>(A); break;
-        case 8: k_rows_lane<MODEL, 8><<<grid, kBlock, smem, s>>>(A); break;
+        case 8:
+            if constexpr (lane_swl_max<MODEL>() >= 8) {
+                k_rows_lane<MODEL, 8><<<grid, kBlock, smem, s>>>(A);
+                break;
+            }
+            return fail(FSGP_EINVAL, "lane kernel slice width");
         default: return fail(FSGP_EINVAL, "lane kernel slice width");
     }
     return FSGP_OK;
@@ -864,7 +912,10 @@ int occupancy_lane(int swl, size_t smem) {
         case 1: z = occupancy_lane_w<MODEL, 1>(smem); break;
         case 2: z = occupancy_lane_w<MODEL, 2>(smem); break;
         case 4: z = occupancy_lane_w<MODEL, 4>(smem); break;
-        default: z = occupancy_lane_w<MODEL, 8>(smem); break;
+        default:
+            if constexpr (lane_swl_max<MODEL>() >= 8) z = occupancy_lane_w<MODEL, 8>(smem);
+            else z = occupancy_lane_w<MODEL, 4>(smem);
+            break;
     }
     return z < 1 ? 1 : z;
 }

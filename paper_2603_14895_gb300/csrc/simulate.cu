@@ -12,6 +12,7 @@
 #include <limits.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <algorithm>
 #include <string>
@@ -23,9 +24,9 @@ namespace fsgp {
 
 // Device-side output pointers of one set.
 struct SetOut {
-    unsigned long long *counts;   // [T+1][3]
-    uint32_t *freq;               // [3][n]
-    uint32_t *per_real;           // [R][T+1][3]
+    unsigned long long *counts;   // [T+1][C]
+    uint32_t *freq;               // [C][n]
+    uint32_t *per_real;           // [R][T+1][C]
     uint32_t *planes;             // [P][n][W]
     int32_t *steps;               // [1] transitions computed (staging in the workspace)
 };
@@ -81,43 +82,49 @@ __global__ void k_import(const uint32_t *__restrict__ in, int planes, int32_t n,
 // recover, a newly active lane stops being new), which dense steps visit through d0_list.
 __global__ void __launch_bounds__(kBlock) k_init_scan(StepArgs A, int model) {
     extern __shared__ int32_t s_lane[];
-    __shared__ unsigned long long s_pc[2 * kMaxSets];
+    __shared__ unsigned long long s_pc[kPC * kMaxSets];
     const int nl = A.Wn * 32;
     const bool lanes_on = A.lane_cnt != nullptr;
     if (lanes_on)
-        for (int i = threadIdx.x; i < 2 * nl; i += blockDim.x) s_lane[i] = 0;
+        for (int i = threadIdx.x; i < A.np * nl; i += blockDim.x) s_lane[i] = 0;
     set_acc_zero(s_pc, A.S);
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     Accum acc;
-    const bool two = model != FSGP_SIS;
+    const int np = A.np;
+    const bool cascade = model == FSGP_IC || model == FSGP_LT;
+    const int e_plane = model == FSGP_SEIR ? 2 : (model == FSGP_SEIS ? 1 : -1);   // exposed lanes
     const bool build = list_wanted(A);
     for (int64_t base = gwarp * 32; base < A.n; base += nwarps * 32) {
         const int64_t v = base + lane;
         const bool has = v < A.n;
-        bool push = false;
+        bool push = false, self = false;
         if (has) {
             for (int w = 0; w < A.Wn; ++w) {
                 const size_t off = (size_t)v * A.Wn + w;
                 const uint32_t s0 = A.cur[off];
-                const uint32_t s1 = two ? A.cur[A.plane_words + off] : 0u;
-                set_acc_add(s_pc, w >> A.ws_shift, __popc(s0), __popc(s1));
+                const uint32_t s1 = np >= 2 ? A.cur[A.plane_words + off] : 0u;
+                const uint32_t s2 = np >= 3 ? A.cur[2 * A.plane_words + off] : 0u;
+                set_acc_add(s_pc, w >> A.ws_shift, __popc(s0), __popc(s1), __popc(s2));
                 if (lanes_on) {
                     lane_deltas(s_lane, w, 0u, s0);
-                    if (two) lane_deltas(s_lane + nl, w, 0u, s1);
+                    if (np >= 2) lane_deltas(s_lane + nl, w, 0u, s1);
+                    if (np >= 3) lane_deltas(s_lane + 2 * nl, w, 0u, s2);
                 }
-                push |= (model == FSGP_SIR || model == FSGP_SIS) ? (s0 != 0u) : (s1 != 0u);
+                push |= cascade ? (s1 != 0u) : (s0 != 0u);
+                if (e_plane >= 0) self |= (e_plane == 2 ? s2 : s1) != 0u;
             }
         }
         if (push) {
             const uint32_t node = node_of(A, (int32_t)v);
             acc.push_deg += (unsigned long long)(A.out_ptr[node + 1] - A.out_ptr[node]);
         }
-        if (has && A.prof_bytes) acc.bytes += (two ? 2ull : 1ull) * 4ull * (unsigned long long)A.Wn;
-        list_append(A, build, has && push, (int32_t)((uint32_t)v | kPushBit), 0);
+        if (has && A.prof_bytes) acc.bytes += (unsigned long long)np * 4ull * (unsigned long long)A.Wn;
+        // rows that push, or whose exposed lanes change on their own, are visited at step 1
+        list_append(A, build, has && (push || self), (int32_t)((uint32_t)v | (push ? kPushBit : 0u)), 0);
         {
-            const bool d0 = has && push && v >= A.r_d0;
+            const bool d0 = has && (push || self) && v >= A.r_d0;
             const unsigned m = __ballot_sync(0xffffffffu, d0);
             if (m) {
                 const int leader = __ffs(m) - 1;
@@ -133,32 +140,44 @@ __global__ void __launch_bounds__(kBlock) k_init_scan(StepArgs A, int model) {
     if (lanes_on) flush_lanes(A, s_lane, nl);
 }
 
-__device__ __forceinline__ void compartments(int model, int64_t total, int64_t p0, int64_t p1,
-                                             int64_t out[3]) {
+// Compartments (C = 3 or 4) from the popcounts p0, p1, p2 of the planes.
+__host__ __device__ __forceinline__ int n_compartments(int model) {
+    return (model == FSGP_SEIR || model == FSGP_SWIR) ? 4 : 3;
+}
+
+__device__ __forceinline__ void compartments(int model, int64_t total, int64_t p0, int64_t p1, int64_t p2,
+                                             int64_t out[4]) {
+    out[3] = 0;
     if (model == FSGP_SIR) {
         out[0] = total - p0 - p1; out[1] = p0; out[2] = p1;
     } else if (model == FSGP_SIS) {
         out[0] = total - p0; out[1] = p0; out[2] = 0;
-    } else {
+    } else if (model == FSGP_SEIR) {          // planes I, R, E -> S, E, I, R
+        out[0] = total - p0 - p1 - p2; out[1] = p2; out[2] = p0; out[3] = p1;
+    } else if (model == FSGP_SEIS) {          // planes I, E -> S, E, I
+        out[0] = total - p0 - p1; out[1] = p1; out[2] = p0;
+    } else if (model == FSGP_SWIR) {          // planes I, R, W -> S, W, I, R
+        out[0] = total - p0 - p1 - p2; out[1] = p2; out[2] = p0; out[3] = p1;
+    } else {                                  // IC / LT: planes A, F
         out[0] = total - p0; out[1] = p1; out[2] = p0 - p1;
     }
 }
 
-// Per-realization snapshot of the running lane counts into per_real[r][kk][3] of every
+// Per-realization snapshot of the running lane counts into per_real[r][kk][C] of every
 // set that asked for it.
 __device__ void snapshot_lanes(const StepArgs &A, int model, const SetOut *outs, int T1, int kk) {
     const int nl = A.Wn * 32;
     const int per_set = A.Ws * 32;
+    const int C = n_compartments(model);
     for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < nl; i += blockDim.x * gridDim.x) {
         const int s = i / per_set, r = i - s * per_set;
         uint32_t *pr = outs[s].per_real;
         if (!pr || r >= A.sp[s].R) continue;
-        int64_t o[3];
-        compartments(model, A.n, A.lane_cnt[i], A.lane_cnt[nl + i], o);
-        uint32_t *dst = pr + ((size_t)r * T1 + kk) * 3;
-        dst[0] = (uint32_t)o[0];
-        dst[1] = (uint32_t)o[1];
-        dst[2] = (uint32_t)o[2];
+        int64_t o[4];
+        compartments(model, A.n, A.lane_cnt[i], A.np >= 2 ? A.lane_cnt[nl + i] : 0,
+                     A.np >= 3 ? A.lane_cnt[2 * nl + i] : 0, o);
+        uint32_t *dst = pr + ((size_t)r * T1 + kk) * C;
+        for (int c = 0; c < C; ++c) dst[c] = (uint32_t)o[c];
     }
 }
 
@@ -169,11 +188,11 @@ __global__ void k_begin(StepArgs A, int model, unsigned long long sparse_limit, 
     if (A.lane_cnt) snapshot_lanes(A, model, outs, T1, A.k - 1);
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     Ctl *C = A.ctl;
-    const unsigned long long *prev = A.pc - 2 * A.S;
-    bool quiet = true;
-    for (int i = 0; i < 2 * A.S; ++i) {
+    const unsigned long long *prev = A.pc - kPC * A.S;
+    bool quiet = true;   // IC / LT: no newly active lane (plane 1) in any set
+    for (int i = 0; i < kPC * A.S; ++i) {
         A.pc[i] = prev[i];
-        if ((i & 1) && prev[i]) quiet = false;
+        if ((i % kPC) == 1 && prev[i]) quiet = false;
     }
     if (C->stop) return;
     if ((model == FSGP_IC || model == FSGP_LT) && quiet) {
@@ -246,25 +265,24 @@ __global__ void __launch_bounds__(kBlock) k_mark(StepArgs A) {
 __global__ void k_finalize(StepArgs A, int model, int T, const unsigned long long *pc_all,
                            const SetOut *outs) {
     const int S = A.S;
+    const int C = n_compartments(model);
     for (int64_t i = threadIdx.x + (int64_t)blockIdx.x * blockDim.x; i < (int64_t)(T + 1) * S;
          i += (int64_t)blockDim.x * gridDim.x) {
         const int k = (int)(i / S), s = (int)(i % S);
-        int64_t o[3];
+        int64_t o[4];
         const int64_t NR = (int64_t)A.n * A.sp[s].R;
-        const unsigned long long *p = pc_all + ((size_t)k * S + s) * 2;
-        compartments(model, NR, (int64_t)p[0], (int64_t)p[1], o);
-        unsigned long long *c = outs[s].counts + 3 * (size_t)k;
-        c[0] = (unsigned long long)o[0];
-        c[1] = (unsigned long long)o[1];
-        c[2] = (unsigned long long)o[2];
+        const unsigned long long *p = pc_all + ((size_t)k * S + s) * kPC;
+        compartments(model, NR, (int64_t)p[0], (int64_t)p[1], (int64_t)p[2], o);
+        unsigned long long *c = outs[s].counts + (size_t)C * k;
+        for (int j = 0; j < C; ++j) c[j] = (unsigned long long)o[j];
     }
     if (A.lane_cnt) snapshot_lanes(A, model, outs, T + 1, T);
-    // IC/LT: the first step whose frontier is empty (later rows repeat); SIR/SIS: T
+    // IC/LT: the first step whose frontier is empty (later rows repeat); otherwise T
     for (int s = threadIdx.x + blockIdx.x * blockDim.x; s < S; s += blockDim.x * gridDim.x) {
         int st = T;
         if (model == FSGP_IC || model == FSGP_LT)
             for (int k = 0; k <= T; ++k)
-                if (pc_all[((size_t)k * S + s) * 2 + 1] == 0ull) {
+                if (pc_all[((size_t)k * S + s) * kPC + 1] == 0ull) {
                     st = k;
                     break;
                 }
@@ -276,7 +294,7 @@ __global__ void k_finalize(StepArgs A, int model, int T, const unsigned long lon
 __global__ void k_freq(StepArgs A, int model, const uint32_t *buf0, const uint32_t *buf1,
                        const SetOut *outs) {
     const uint32_t *st = (A.ctl->steps_done & 1) ? buf1 : buf0;
-    const bool two = model != FSGP_SIS;
+    const int np = A.np, C = n_compartments(model);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t v = node_of(A, (int32_t)i);   // row i holds node v
@@ -284,17 +302,16 @@ __global__ void k_freq(StepArgs A, int model, const uint32_t *buf0, const uint32
             uint32_t *fr = outs[s].freq;
             if (!fr) continue;
             const int W = A.sp[s].W;
-            int64_t p0 = 0, p1 = 0;
+            int64_t p0 = 0, p1 = 0, p2 = 0;
             for (int w = 0; w < W; ++w) {
                 const size_t off = (size_t)i * A.Wn + (size_t)s * A.Ws + w;
                 p0 += __popc(st[off]);
-                if (two) p1 += __popc(st[A.plane_words + off]);
+                if (np >= 2) p1 += __popc(st[A.plane_words + off]);
+                if (np >= 3) p2 += __popc(st[2 * A.plane_words + off]);
             }
-            int64_t o[3];
-            compartments(model, A.sp[s].R, p0, p1, o);
-            fr[v] = (uint32_t)o[0];
-            fr[(size_t)A.n + v] = (uint32_t)o[1];
-            fr[2 * (size_t)A.n + v] = (uint32_t)o[2];
+            int64_t o[4];
+            compartments(model, A.sp[s].R, p0, p1, p2, o);
+            for (int c = 0; c < C; ++c) fr[(size_t)c * A.n + v] = (uint32_t)o[c];
         }
     }
 }
@@ -391,7 +408,11 @@ static int launch_rows_model(int model, const StepArgs &A, const StepLaunch &L, 
         case FSGP_SIR: return launch_rows<FSGP_SIR>(A, L, s);
         case FSGP_SIS: return launch_rows<FSGP_SIS>(A, L, s);
         case FSGP_IC: return launch_rows<FSGP_IC>(A, L, s);
-        default: return launch_rows<FSGP_LT>(A, L, s);
+        case FSGP_LT: return launch_rows<FSGP_LT>(A, L, s);
+        case FSGP_SEIR: return launch_rows<FSGP_SEIR>(A, L, s);
+        case FSGP_SEIS: return launch_rows<FSGP_SEIS>(A, L, s);
+        case FSGP_SWIR: return launch_rows<FSGP_SWIR>(A, L, s);
+        default: return fail(FSGP_EINVAL, "model without row kernels");
     }
 }
 
@@ -400,7 +421,11 @@ static int occupancy_model(int model, int V, int TEAM, size_t smem, RowOccupancy
         case FSGP_SIR: return occupancy_rows<FSGP_SIR>(V, TEAM, smem, o);
         case FSGP_SIS: return occupancy_rows<FSGP_SIS>(V, TEAM, smem, o);
         case FSGP_IC: return occupancy_rows<FSGP_IC>(V, TEAM, smem, o);
-        default: return occupancy_rows<FSGP_LT>(V, TEAM, smem, o);
+        case FSGP_LT: return occupancy_rows<FSGP_LT>(V, TEAM, smem, o);
+        case FSGP_SEIR: return occupancy_rows<FSGP_SEIR>(V, TEAM, smem, o);
+        case FSGP_SEIS: return occupancy_rows<FSGP_SEIS>(V, TEAM, smem, o);
+        case FSGP_SWIR: return occupancy_rows<FSGP_SWIR>(V, TEAM, smem, o);
+        default: return fail(FSGP_EINVAL, "model without row kernels");
     }
 }
 
@@ -435,6 +460,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
                     int Ws, int T, const fsgp_options &opt, cudaStream_t s) {
     const int32_t n = g->n;
     const int P = fsgp_model_planes(model);
+    const int C = n_compartments(model);
     const int Wn = S * Ws;
     const int pd = Ws << __builtin_ctz((unsigned)S);   // largest power of two dividing Wn
     int V = opt.vector_words ? opt.vector_words : 2;   // 2 measured best on GB300
@@ -447,7 +473,8 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     if (opt.lane_words != 0 && opt.lane_words != 1 && opt.lane_words != 2 && opt.lane_words != 4 &&
         opt.lane_words != 8)
         return fail(FSGP_EINVAL, "lane_words must be 1, 2, 4 or 8");
-    const int lane_swl = std::min(opt.lane_words > 0 ? opt.lane_words : 8, pd);
+    // (three-plane models stage at most 4 words per thread)
+    const int lane_swl = std::min(std::min(opt.lane_words > 0 ? opt.lane_words : 8, P >= 3 ? 4 : 8), pd);
     const bool host_out = sets[0]->out_flags == FSGP_PTR_HOST;
     bool want_lanes = false, want_freq = false, any_init = false, want_steps = false;
     for (int i = 0; i < S; ++i) {
@@ -494,17 +521,29 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
 
     // per-set parameters and survival tables
     std::vector<uint64_t> surv_all;
-    std::vector<size_t> surv_off((size_t)S);
+    std::vector<size_t> surv_off((size_t)S), survmu_off((size_t)S), survnu_off((size_t)S);
     std::vector<SetParams> hp((size_t)S);
     int64_t seeds_total = 0, preal_total = 0, planes_total = 0;
     std::vector<int64_t> seed_off((size_t)S), preal_off((size_t)S), planes_off((size_t)S);
+    const bool infection_table = model == FSGP_SIR || model == FSGP_SIS || model == FSGP_SEIR ||
+                                 model == FSGP_SEIS || model == FSGP_SWIR;
     for (int i = 0; i < S; ++i) {
         const SetSpec &x = *sets[i];
         SetParams &p = hp[i];
+        p = SetParams{};
         surv_off[i] = surv_all.size();
         int32_t ksat = INT32_MAX;
-        if (model == FSGP_SIR || model == FSGP_SIS) survival_table(x.beta, g->max_deg, surv_all, &ksat);
+        if (infection_table) survival_table(x.beta, g->max_deg, surv_all, &ksat);
         else surv_all.push_back(TWO32);
+        survmu_off[i] = survnu_off[i] = surv_off[i];
+        p.ksat_mu = p.ksat_nu = ksat;
+        if (model == FSGP_SWIR) {
+            survmu_off[i] = surv_all.size();
+            survival_table(x.mu, g->max_deg, surv_all, &p.ksat_mu);
+            survnu_off[i] = surv_all.size();
+            survival_table(x.nu, g->max_deg, surv_all, &p.ksat_nu);
+        }
+        p.a_lat = (uint64_t)llrint(x.alpha * 4294967296.0);
         p.key0 = (uint32_t)(x.rng_seed & 0xffffffffu);
         p.key1 = (uint32_t)(x.rng_seed >> 32);
         p.ksat = ksat;
@@ -516,7 +555,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
         seed_off[i] = seeds_total;
         if (!x.init_planes && x.seed_flags == FSGP_PTR_HOST) seeds_total += x.n_seeds;
         preal_off[i] = preal_total;
-        if (x.per_real) preal_total += (int64_t)x.R * (T + 1) * 3;
+        if (x.per_real) preal_total += (int64_t)x.R * (T + 1) * C;
         planes_off[i] = planes_total;
         if (x.final_planes || x.init_planes) planes_total += (int64_t)P * n * p.W;
     }
@@ -529,18 +568,18 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
            O_STEPS, O_D0, O_HUBSAT, O_END };
     size_t sz[O_END] = {0};
     sz[O_STATE] = 2 * state_words * sizeof(uint32_t);
-    sz[O_PC] = T1 * S * 2 * sizeof(unsigned long long);
+    sz[O_PC] = T1 * S * kPC * sizeof(unsigned long long);
     sz[O_CTL] = sizeof(Ctl);
     // a row is listed once per work item: slices of the team kernels or of the lane kernel
     sz[O_LIST0] = sz[O_LIST1] = (size_t)n * std::max(nslices, Wn / lane_swl) * sizeof(int32_t);
     sz[O_CSMALL] = sz[O_CMID] = (size_t)n * sizeof(int32_t);
     sz[O_BITMAP] = ((size_t)n + 31) / 32 * sizeof(uint32_t);
-    sz[O_LANES] = want_lanes ? 2 * (size_t)Wn * 32 * sizeof(int32_t) : 0;
+    sz[O_LANES] = want_lanes ? (size_t)P * Wn * 32 * sizeof(int32_t) : 0;
     sz[O_HUB] = (size_t)n_hubs * Wn * 32 * sizeof(uint32_t);
     sz[O_SURV] = surv_all.size() * sizeof(uint64_t);
     sz[O_SEEDS] = (size_t)seeds_total * sizeof(int32_t);
-    sz[O_COUNTS] = host_out ? T1 * 3 * S * sizeof(uint64_t) : 0;
-    sz[O_FREQ] = (host_out && want_freq) ? 3 * (size_t)n * S * sizeof(uint32_t) : 0;
+    sz[O_COUNTS] = host_out ? T1 * C * S * sizeof(uint64_t) : 0;
+    sz[O_FREQ] = (host_out && want_freq) ? (size_t)C * n * S * sizeof(uint32_t) : 0;
     sz[O_PREAL] = host_out ? (size_t)preal_total * sizeof(uint32_t) : 0;
     sz[O_PLANES] = (host_out || any_init) ? (size_t)planes_total * sizeof(uint32_t) : 0;
     sz[O_PROF] = FSGP_PROF_KINDS * sizeof(unsigned long long);
@@ -548,7 +587,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     sz[O_OUT] = (size_t)S * sizeof(SetOut);
     sz[O_STEPS] = (size_t)S * sizeof(int32_t);
     sz[O_D0] = (size_t)n_d0 * sizeof(int32_t);
-    const bool hub_sat = model == FSGP_SIR || model == FSGP_SIS;
+    const bool hub_sat = model == FSGP_SIR || model == FSGP_SIS || model == FSGP_SEIR || model == FSGP_SEIS;
     sz[O_HUBSAT] = hub_sat ? (size_t)n_hubs * nslices * sizeof(uint32_t) : 0;
     size_t off[O_END], total = 0;
     for (int i = 0; i < O_END; ++i) {
@@ -569,7 +608,11 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     SetParams *d_sp = (SetParams *)(ws + off[O_SP]);
     SetOut *d_out = (SetOut *)(ws + off[O_OUT]);
     int32_t *d_steps = (int32_t *)(ws + off[O_STEPS]);
-    for (int i = 0; i < S; ++i) hp[i].surv = d_surv + surv_off[i];
+    for (int i = 0; i < S; ++i) {
+        hp[i].surv = d_surv + surv_off[i];
+        hp[i].surv_mu = d_surv + survmu_off[i];
+        hp[i].surv_nu = d_surv + survnu_off[i];
+    }
     FSGP_CUDA(cudaMemcpyAsync(d_surv, surv_all.data(), sz[O_SURV], cudaMemcpyHostToDevice, s));
     FSGP_CUDA(cudaMemcpyAsync(d_sp, hp.data(), sz[O_SP], cudaMemcpyHostToDevice, s));
     // device output pointers of each set (caller memory, or staging for host results)
@@ -578,8 +621,8 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
         const SetSpec &x = *sets[i];
         SetOut &o = ho[i];
         if (host_out) {
-            o.counts = (unsigned long long *)(ws + off[O_COUNTS]) + (size_t)i * T1 * 3;
-            o.freq = x.freq ? (uint32_t *)(ws + off[O_FREQ]) + (size_t)i * 3 * n : nullptr;
+            o.counts = (unsigned long long *)(ws + off[O_COUNTS]) + (size_t)i * T1 * C;
+            o.freq = x.freq ? (uint32_t *)(ws + off[O_FREQ]) + (size_t)i * C * n : nullptr;
             o.per_real = x.per_real ? (uint32_t *)(ws + off[O_PREAL]) + preal_off[i] : nullptr;
             o.planes = x.final_planes ? (uint32_t *)(ws + off[O_PLANES]) + planes_off[i] : nullptr;
         } else {
@@ -593,7 +636,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     FSGP_CUDA(cudaMemcpyAsync(d_out, ho.data(), sz[O_OUT], cudaMemcpyHostToDevice, s));
 
     // ---------------------------------------------------------------- launch shape
-    const size_t smem_lanes = want_lanes ? 2 * (size_t)Wn * 32 * sizeof(int32_t) : 0;
+    const size_t smem_lanes = want_lanes ? (size_t)P * Wn * 32 * sizeof(int32_t) : 0;
     if (smem_lanes > 32 * 1024) return fail(FSGP_EINVAL, "per-lane counters exceed shared memory");
     RowOccupancy occ{};
     occ.swl = lane_swl;
@@ -656,6 +699,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     A.ic_mode = ic_mode;
     A.ctl = ctl;
     A.lane_cnt = want_lanes ? (int32_t *)(ws + off[O_LANES]) : nullptr;
+    A.np = P;
     A.r_small = start_small;
     A.n_small = n_small;
     A.r_small4 = std::max(start_small4, start_small);
@@ -717,7 +761,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
                 sd = stage;
             }
             k_seed<<<grid_cap(x.n_seeds * Ws, 256, g->sm_count, 16), 256, 0, s>>>(
-                buf0, buf1, A.plane_words, model != FSGP_SIR && model != FSGP_SIS, sd, x.n_seeds,
+                buf0, buf1, A.plane_words, model == FSGP_IC || model == FSGP_LT, sd, x.n_seeds,
                 g->pos, Wn, ws0, Ws, hp[i].W, hp[i].last_mask);
             ++launches;
         }
@@ -727,7 +771,6 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     // (the legacy default stream cannot be captured; such callers launch directly)
     const bool capture = opt.capture_graph != 0 && !profiling && s != nullptr && s != cudaStreamLegacy &&
                          s != cudaStreamPerThread;
-    if (capture) FSGP_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     // step 0
     A.cur = buf0;
     A.nxt = buf1;
@@ -736,6 +779,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     A.t = (uint32_t)opt.t0;
     A.list_in = list[1];
     A.list_out = list[0];
+    if (capture) FSGP_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     k_init_scan<<<grid_scan, kBlock, smem_lanes, s>>>(A, model);
     ++launches;
     if (profiling) prof.stop(s);
@@ -745,7 +789,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
         A.t = (uint32_t)(opt.t0 + k);
         A.cur = (k & 1) ? buf0 : buf1;
         A.nxt = (k & 1) ? buf1 : buf0;
-        A.pc = pc + (size_t)k * S * 2;
+        A.pc = pc + (size_t)k * S * kPC;
         A.list_in = list[(k - 1) & 1];
         A.list_out = list[k & 1];
         const int force_dense = !allow_sparse || (k == 1 && any_init && model == FSGP_LT);
@@ -807,11 +851,11 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     if (host_out) {
         for (int i = 0; i < S; ++i) {
             const SetSpec &x = *sets[i];
-            FSGP_CUDA(cudaMemcpyAsync(x.counts, ho[i].counts, T1 * 3 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+            FSGP_CUDA(cudaMemcpyAsync(x.counts, ho[i].counts, T1 * C * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
             if (x.freq)
-                FSGP_CUDA(cudaMemcpyAsync(x.freq, ho[i].freq, 3 * (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+                FSGP_CUDA(cudaMemcpyAsync(x.freq, ho[i].freq, (size_t)C * n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
             if (x.per_real)
-                FSGP_CUDA(cudaMemcpyAsync(x.per_real, ho[i].per_real, (size_t)x.R * T1 * 3 * sizeof(uint32_t),
+                FSGP_CUDA(cudaMemcpyAsync(x.per_real, ho[i].per_real, (size_t)x.R * T1 * C * sizeof(uint32_t),
                                           cudaMemcpyDeviceToHost, s));
             if (x.final_planes)
                 FSGP_CUDA(cudaMemcpyAsync(x.final_planes, ho[i].planes, (size_t)P * n * hp[i].W * sizeof(uint32_t),
@@ -855,7 +899,7 @@ int run_sets(fsgp_graph *g, int model, int ic_mode, const SetSpec *sets, int n_s
         if (!x.counts) return fail(FSGP_EINVAL, "result counts buffer is NULL");
         if (x.out_flags != of) return fail(FSGP_EINVAL, "all result buffers of one call must be host or all device");
         auto bad_p = [](double p) { return !(p >= 0.0 && p <= 1.0); };
-        if (bad_p(x.beta) || bad_p(x.gamma) || bad_p(x.ic_p))
+        if (bad_p(x.beta) || bad_p(x.gamma) || bad_p(x.ic_p) || bad_p(x.alpha) || bad_p(x.mu) || bad_p(x.nu))
             return fail(FSGP_EINVAL, "probabilities must lie in [0, 1]");
         if (!x.init_planes && x.n_seeds > 0) {
             if (!x.seeds) return fail(FSGP_EINVAL, "seed_nodes is NULL");
@@ -891,7 +935,8 @@ int run_sets(fsgp_graph *g, int model, int ic_mode, const SetSpec *sets, int n_s
         while (i < order.size() && words_per_set(sets[order[i]].R) == Ws && (int)wave.size() < smax) {
             const SetSpec *x = &sets[order[i]];
             const bool l2 = lanes || x->per_real;
-            if (l2 && !wave.empty() && (int)(wave.size() + 1) * Ws > 128) break;   // 32 KB of lane counters
+            // 32 KB of lane counters: planes x words x 32 lanes x 4 B
+            if (l2 && !wave.empty() && (int)(wave.size() + 1) * Ws * P > 256) break;
             lanes = l2;
             wave.push_back(x);
             ++i;
@@ -914,7 +959,7 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
     set_error("");
     fsgp_graph *g = const_cast<fsgp_graph *>(gc);
     if (!g) return fail(FSGP_EINVAL, "graph is NULL");
-    if (model < FSGP_SIR || model > FSGP_LT) return fail(FSGP_EINVAL, "unknown model");
+    if (model < FSGP_SIR || model > FSGP_SWIR) return fail(FSGP_EINVAL, "unknown model");
     if (!params) return fail(FSGP_EINVAL, "params is NULL");
     if (!out || !out->counts) return fail(FSGP_EINVAL, "result counts buffer is NULL");
     if (out->flags != FSGP_PTR_HOST && out->flags != FSGP_PTR_DEVICE)
@@ -942,15 +987,22 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
     FSGP_CUDA(cudaGetDevice(&dev));
     if (dev != g->device) return fail(FSGP_EINVAL, "current device differs from the graph's device");
     const int P = fsgp_model_planes(model);
+    const int C = n_compartments(model);
     const int W = (R + 31) / 32;
     const size_t T1 = (size_t)T + 1;
+    // SI is SIS without recovery: the same planes, draws and compartments
+    const bool si = model == FSGP_SI;
+    const int run_model = si ? FSGP_SIS : model;
     std::vector<SetSpec> sets((size_t)n_sets);
     for (int i = 0; i < n_sets; ++i) {
         SetSpec &x = sets[i];
         x = SetSpec{};
         x.beta = params->beta;
-        x.gamma = params->gamma;
+        x.gamma = si ? 0.0 : params->gamma;
         x.ic_p = params->ic_p;
+        x.alpha = params->alpha;
+        x.mu = params->mu;
+        x.nu = params->nu;
         x.rng_seed = rng_seed;
         x.R = R;
         if (use_init) {
@@ -960,12 +1012,12 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
             x.n_seeds = seed_offsets[i + 1] - seed_offsets[i];
             x.seed_flags = seed_flags;
         }
-        x.counts = out->counts + (size_t)i * T1 * 3;
-        x.freq = out->freq ? out->freq + (size_t)i * 3 * g->n : nullptr;
-        x.per_real = out->per_real ? out->per_real + (size_t)i * R * T1 * 3 : nullptr;
+        x.counts = out->counts + (size_t)i * T1 * C;
+        x.freq = out->freq ? out->freq + (size_t)i * C * g->n : nullptr;
+        x.per_real = out->per_real ? out->per_real + (size_t)i * R * T1 * C : nullptr;
         x.final_planes = out->final_planes ? out->final_planes + (size_t)i * P * g->n * W : nullptr;
         x.steps_run = out->steps_run ? out->steps_run + i : nullptr;
         x.out_flags = out->flags;
     }
-    return run_sets(g, model, params->ic_mode, sets.data(), n_sets, T, opt, (cudaStream_t)stream);
+    return run_sets(g, run_model, params->ic_mode, sets.data(), n_sets, T, opt, (cudaStream_t)stream);
 }

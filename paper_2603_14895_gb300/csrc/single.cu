@@ -234,6 +234,8 @@ extern "C" int fsgp_simulate_single(const fsgp_graph *gc, int32_t model, const f
     set_error("");
     fsgp_graph *g = const_cast<fsgp_graph *>(gc);   // the cached workspace is grown
     if (!g || !params || !counts) return fail(FSGP_EINVAL, "NULL argument");
+    if (model > FSGP_LT && model <= FSGP_SWIR)
+        return fail(FSGP_EUNSUPPORTED, "this entry point covers the SIR, SIS, IC and LT models");
     if (model < FSGP_SIR || model > FSGP_LT) return fail(FSGP_EINVAL, "unknown model");
     if (r < 0 || T < 0 || n_seeds < 0 || (n_seeds > 0 && !seed_nodes)) return fail(FSGP_EINVAL, "bad r, T or seeds");
     if (seed_flags > FSGP_PTR_DEVICE || out_flags > FSGP_PTR_DEVICE) return fail(FSGP_EINVAL, "bad flags");

@@ -55,7 +55,15 @@ struct SetParams {
     int32_t R;
     uint64_t g_rec;                 // recovery threshold
     uint64_t p_const;               // IC constant threshold
+    uint64_t a_lat;                 // SEIR/SEIS: exposed -> infectious threshold
+    const uint64_t *surv_mu;        // SWIR: weakening survival table, and its K_sat
+    int32_t ksat_mu;
+    const uint64_t *surv_nu;        // SWIR: survival table of weakened lanes, and its K_sat
+    int32_t ksat_nu;
 };
+
+// Running plane popcounts are kept for up to three planes per set.
+constexpr int kPC = 3;
 
 // Row ids are "new ids": the graph's rows relabelled in degree-bucket order (row i of
 // the state planes is node orig[i]).  Random draws are keyed by the node (Philox subject)
@@ -90,8 +98,9 @@ struct StepArgs {
     int32_t k;             // relative step index (1..T)
     // control and accumulators
     Ctl *ctl;
-    unsigned long long *pc;        // [S][2] plane popcounts of this step (running totals)
-    int32_t *lane_cnt;             // [2][Wn*32] running per-lane plane counts, or null
+    unsigned long long *pc;        // [S][kPC] plane popcounts of this step (running totals)
+    int32_t *lane_cnt;             // [planes][Wn*32] running per-lane plane counts, or null
+    int32_t np;                    // planes of the model
     // dense steps: row classes as new-id ranges: small rows by in-degree class (16..,
     // 4..15, 1..3), mid rows; rows without in-arcs only through d0_list
     int32_t r_small, n_small, r_small4, n_small4, r_lane, n_lane, r_mid, n_mid;
@@ -388,7 +397,7 @@ __device__ __forceinline__ uint32_t grouped_u_less(const uint32_t (&c)[B], uint3
 // ------------------------------------------------------- per-word update (Eq. updata)
 
 struct WordOut {
-    uint32_t n0, n1;
+    uint32_t n0, n1, n2;
 };
 
 // SIR / SIS word update from counts of infected in-arcs (Appendix A.1 rules).
@@ -420,6 +429,77 @@ __device__ __forceinline__ WordOut update_sir_word(const StepArgs &A, uint32_t v
     WordOut o;
     o.n0 = (s0 & ~rec) | infect;
     o.n1 = MODEL == FSGP_SIR ? (s1 | rec) : 0u;
+    o.n2 = 0u;
+    return o;
+}
+
+// Lanes of `cand` (susceptible lanes with k >= 1) whose uniform u(tag) reaches the
+// survival threshold surv[k] of a table with first zero at K_sat (d: in-degree).
+template <int B>
+__device__ __forceinline__ uint32_t surv_reached(const StepArgs &A, uint32_t v, const WordCtx &x, uint32_t cand,
+                                                 int32_t d, const uint32_t (&c)[B], const uint64_t *surv,
+                                                 int32_t ksat, uint32_t tag) {
+    if (!cand) return 0u;
+    uint32_t sat = 0u;
+    if ((uint64_t)ksat < (1ull << B)) sat = ge_const<B>(c, (uint32_t)ksat) & cand;
+    const uint32_t rem = cand & ~sat;
+    uint32_t below = 0u;
+    if (rem) {
+        const uint32_t kcap = (uint32_t)min(d, ksat - 1);
+        below = grouped_u_less<B>(c, rem, [surv](uint32_t k) { return __ldg(surv + k); }, kcap, v, A.t, x.g,
+                                  tag, x.k0, x.k1);
+    }
+    return sat | (rem & ~below);
+}
+
+// SEIR / SEIS word update (the discrete-time rows of Table 1): planes I (s0) and, SEIR:
+// R (s1), E (s2); SEIS: E (s1).  S -> E with the infection rule, E -> I with alpha
+// (tag 5), I -> R (SEIS: S) with gamma; one change per lane and step.
+template <int MODEL, int B>
+__device__ __forceinline__ WordOut update_seir_word(const StepArgs &A, uint32_t v, const WordCtx &x,
+                                                    uint32_t s0, uint32_t s1, uint32_t s2, int32_t d,
+                                                    const uint32_t (&c)[B]) {
+    const SetParams &p = A.sp[x.s];
+    const uint32_t I = s0 & x.vm;
+    const uint32_t E = (MODEL == FSGP_SEIR ? s2 : s1) & x.vm;
+    const uint32_t Rm = MODEL == FSGP_SEIR ? (s1 & x.vm) : 0u;
+    const uint32_t S = x.vm & ~I & ~E & ~Rm;
+    const uint32_t expose = surv_reached<B>(A, v, x, S & any_count<B>(c), d, c, p.surv, __ldg(&p.ksat), TAG_INFECT);
+    const uint32_t lat = lanes_u_less(E, __ldg(&p.a_lat), v, A.t, x.g, TAG_LATENT, x.k0, x.k1);
+    const uint32_t rec = lanes_u_less(I, __ldg(&p.g_rec), v, A.t, x.g, TAG_RECOVER, x.k0, x.k1);
+    const uint32_t nI = (I & ~rec) | lat;
+    const uint32_t nE = (E & ~lat) | expose;
+    WordOut o;
+    o.n0 = nI;
+    if (MODEL == FSGP_SEIR) {
+        o.n1 = Rm | rec;
+        o.n2 = nE;
+    } else {
+        o.n1 = nE;
+        o.n2 = 0u;
+    }
+    return o;
+}
+
+// SWIR word update: planes I (s0), R (s1), W (s2).  A susceptible lane with k >= 1 is
+// infected with the kappa table (tag 1), otherwise weakened with the mu table (tag 6); a
+// weakened lane with k >= 1 is infected with the nu table (tag 1); I -> R after a step.
+template <int B>
+__device__ __forceinline__ WordOut update_swir_word(const StepArgs &A, uint32_t v, const WordCtx &x,
+                                                    uint32_t s0, uint32_t s1, uint32_t s2, int32_t d,
+                                                    const uint32_t (&c)[B]) {
+    const SetParams &p = A.sp[x.s];
+    const uint32_t I = s0 & x.vm, Rm = s1 & x.vm, Wk = s2 & x.vm;
+    const uint32_t S = x.vm & ~I & ~Rm & ~Wk;
+    const uint32_t pressed = any_count<B>(c);
+    const uint32_t infS = surv_reached<B>(A, v, x, S & pressed, d, c, p.surv, __ldg(&p.ksat), TAG_INFECT);
+    const uint32_t weak = surv_reached<B>(A, v, x, S & pressed & ~infS, d, c, p.surv_mu, __ldg(&p.ksat_mu),
+                                          TAG_WEAKEN);
+    const uint32_t infW = surv_reached<B>(A, v, x, Wk & pressed, d, c, p.surv_nu, __ldg(&p.ksat_nu), TAG_INFECT);
+    WordOut o;
+    o.n0 = infS | infW;
+    o.n1 = Rm | I;
+    o.n2 = (Wk & ~infW) | weak;
     return o;
 }
 
@@ -444,6 +524,7 @@ __device__ __forceinline__ WordOut update_lt_word(const StepArgs &A, uint32_t v,
     WordOut o;
     o.n0 = s0 | act;
     o.n1 = act;
+    o.n2 = 0u;
     return o;
 }
 
@@ -459,18 +540,20 @@ struct Accum {
 constexpr int kMaxSets = 128;
 
 __device__ __forceinline__ void set_acc_zero(unsigned long long *s_pc, int S) {
-    for (int i = threadIdx.x; i < 2 * S; i += blockDim.x) s_pc[i] = 0ull;
+    for (int i = threadIdx.x; i < kPC * S; i += blockDim.x) s_pc[i] = 0ull;
     __syncthreads();
 }
 
-__device__ __forceinline__ void set_acc_add(unsigned long long *s_pc, int s, long long d0, long long d1) {
-    if (d0) atomicAdd(&s_pc[2 * s], (unsigned long long)d0);
-    if (d1) atomicAdd(&s_pc[2 * s + 1], (unsigned long long)d1);
+__device__ __forceinline__ void set_acc_add(unsigned long long *s_pc, int s, long long d0, long long d1,
+                                            long long d2 = 0) {
+    if (d0) atomicAdd(&s_pc[kPC * s], (unsigned long long)d0);
+    if (d1) atomicAdd(&s_pc[kPC * s + 1], (unsigned long long)d1);
+    if (d2) atomicAdd(&s_pc[kPC * s + 2], (unsigned long long)d2);
 }
 
 // after a __syncthreads of the caller
 __device__ __forceinline__ void set_acc_flush(const StepArgs &A, const unsigned long long *s_pc) {
-    for (int i = threadIdx.x; i < 2 * A.S; i += blockDim.x)
+    for (int i = threadIdx.x; i < kPC * A.S; i += blockDim.x)
         if (s_pc[i]) atomicAdd(&A.pc[i], s_pc[i]);
 }
 
@@ -517,7 +600,7 @@ __device__ __forceinline__ void flush_accum(const StepArgs &A, Accum acc, int li
 // per-CTA lane counters (shared memory) -> global running lane counts
 __device__ __forceinline__ void flush_lanes(const StepArgs &A, int32_t *s_lane, int nl) {
     __syncthreads();
-    for (int i = threadIdx.x; i < 2 * nl; i += blockDim.x) {
+    for (int i = threadIdx.x; i < A.np * nl; i += blockDim.x) {
         const int32_t x = s_lane[i];
         if (x) atomicAdd(&A.lane_cnt[i], x);
     }
@@ -570,16 +653,16 @@ struct Prof {
 // One seed set (or one batched request) of a run: parameters, inputs and caller-owned
 // outputs (memory kind out_flags; NULL = not wanted, except counts).
 struct SetSpec {
-    double beta, gamma, ic_p;
+    double beta, gamma, ic_p, alpha, mu, nu;
     uint64_t rng_seed;
     int32_t R;
     const int32_t *seeds;          // seed nodes (memory kind seed_flags)
     int64_t n_seeds;
     uint32_t seed_flags;
     const uint32_t *init_planes;   // optional start planes [P][n][ceil(R/32)]
-    uint64_t *counts;              // [T+1][3]
-    uint32_t *freq;                // [3][n]
-    uint32_t *per_real;            // [R][T+1][3]
+    uint64_t *counts;              // [T+1][C]
+    uint32_t *freq;                // [C][n]
+    uint32_t *per_real;            // [R][T+1][C]
     uint32_t *final_planes;        // [P][n][ceil(R/32)]
     int32_t *steps_run;            // [1]
     uint32_t out_flags;

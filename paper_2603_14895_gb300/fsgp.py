@@ -20,6 +20,7 @@ _lib = None
 FSGP_OK = 0
 FSGP_EINVAL, FSGP_ENOMEM, FSGP_ECUDA, FSGP_EUNSUPPORTED = -1, -2, -3, -5
 SIR, SIS, IC, LT = 0, 1, 2, 3
+SI, SEIR, SEIS, SWIR = 4, 5, 6, 7
 PTR_HOST, PTR_DEVICE = 0, 1
 IC_WEIGHTED_CASCADE, IC_CONSTANT = 0, 1
 
@@ -32,7 +33,8 @@ class FsgpError(RuntimeError):
 
 class fsgp_params(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("gamma", ctypes.c_double),
-                ("ic_mode", ctypes.c_int32), ("ic_p", ctypes.c_double)]
+                ("ic_mode", ctypes.c_int32), ("ic_p", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("mu", ctypes.c_double), ("nu", ctypes.c_double)]
 
 
 PROF_KINDS = 10
@@ -106,6 +108,8 @@ def load():
         lib.fsgp_graph_trim.restype = ctypes.c_int
         lib.fsgp_model_planes.argtypes = [ctypes.c_int32]
         lib.fsgp_model_planes.restype = ctypes.c_int
+        lib.fsgp_model_compartments.argtypes = [ctypes.c_int32]
+        lib.fsgp_model_compartments.restype = ctypes.c_int
         lib.fsgp_simulate.argtypes = [P, ctypes.c_int32, ctypes.POINTER(fsgp_params), P, P,
                                       ctypes.c_int32, ctypes.c_uint32, ctypes.c_int32,
                                       ctypes.c_int32, ctypes.c_uint64,
@@ -181,6 +185,13 @@ def fsgp_last_error() -> str:
 
 def fsgp_version() -> int:
     return load().fsgp_version()
+
+
+def fsgp_model_compartments(model: int) -> int:
+    c = load().fsgp_model_compartments(model)
+    if c < 0:
+        raise FsgpError(c, load().fsgp_last_error().decode())
+    return c
 
 
 def fsgp_model_planes(model: int) -> int:
@@ -300,9 +311,9 @@ def make_options(**kw) -> fsgp_options:
 
 
 def simulate(graph: Graph, model: int, seed_sets, R: int, T: int, rng_seed: int, *, beta=0.0,
-             gamma=0.0, ic_mode=IC_WEIGHTED_CASCADE, ic_p=0.0, freq=True, per_real=False,
-             final_planes=False, steps_run=True, device=True, options=None, stream=None,
-             out=None):
+             gamma=0.0, ic_mode=IC_WEIGHTED_CASCADE, ic_p=0.0, alpha=0.0, mu=0.0, nu=0.0,
+             freq=True, per_real=False, final_planes=False, steps_run=True, device=True,
+             options=None, stream=None, out=None):
     """Run fsgp_simulate; results are torch tensors on the current CUDA device
     (device=True) or numpy arrays (device=False)."""
     import torch
@@ -316,6 +327,7 @@ def simulate(graph: Graph, model: int, seed_sets, R: int, T: int, rng_seed: int,
     seeds = np.concatenate([np.asarray(s, dtype=np.int32) for s in seed_sets]) if offs[-1] \
         else np.zeros(1, dtype=np.int32)
     P = fsgp_model_planes(model)
+    C = fsgp_model_compartments(model)
     W = (R + 31) // 32
     T1 = T + 1
     if out is None:
@@ -323,21 +335,21 @@ def simulate(graph: Graph, model: int, seed_sets, R: int, T: int, rng_seed: int,
         if device:
             dev = torch.device("cuda", torch.cuda.current_device())
             mk = lambda shape, dt: torch.zeros(shape, dtype=dt, device=dev)  # noqa: E731
-            out["counts"] = mk((n_sets, T1, 3), torch.int64)
+            out["counts"] = mk((n_sets, T1, C), torch.int64)
             if freq:
-                out["freq"] = mk((n_sets, 3, n), torch.int32)
+                out["freq"] = mk((n_sets, C, n), torch.int32)
             if per_real:
-                out["per_real"] = mk((n_sets, R, T1, 3), torch.int32)
+                out["per_real"] = mk((n_sets, R, T1, C), torch.int32)
             if final_planes:
                 out["final_planes"] = mk((n_sets, P, n, W), torch.int32)
             if steps_run:
                 out["steps_run"] = mk((n_sets,), torch.int32)
         else:
-            out["counts"] = np.zeros((n_sets, T1, 3), dtype=np.uint64)
+            out["counts"] = np.zeros((n_sets, T1, C), dtype=np.uint64)
             if freq:
-                out["freq"] = np.zeros((n_sets, 3, n), dtype=np.uint32)
+                out["freq"] = np.zeros((n_sets, C, n), dtype=np.uint32)
             if per_real:
-                out["per_real"] = np.zeros((n_sets, R, T1, 3), dtype=np.uint32)
+                out["per_real"] = np.zeros((n_sets, R, T1, C), dtype=np.uint32)
             if final_planes:
                 out["final_planes"] = np.zeros((n_sets, P, n, W), dtype=np.uint32)
             if steps_run:
@@ -349,7 +361,7 @@ def simulate(graph: Graph, model: int, seed_sets, R: int, T: int, rng_seed: int,
     res.per_real = _ptr(out.get("per_real"))
     res.final_planes = _ptr(out.get("final_planes"))
     res.steps_run = _ptr(out.get("steps_run"))
-    prm = fsgp_params(beta=beta, gamma=gamma, ic_mode=ic_mode, ic_p=ic_p)
+    prm = fsgp_params(beta=beta, gamma=gamma, ic_mode=ic_mode, ic_p=ic_p, alpha=alpha, mu=mu, nu=nu)
     if isinstance(options, dict):
         options = make_options(**options)
     fsgp_simulate(graph.handle, model, prm, seeds, offs, n_sets, PTR_HOST, R, T, rng_seed,
@@ -392,18 +404,20 @@ def batch_run(requests, *, n_streams=0, capture_graph=0, autotune=0, stream=None
         seeds = np.ascontiguousarray(rq.get("seeds", np.zeros(0, np.int32)), dtype=np.int32)
         keep.append(seeds)
         R, T, model = int(rq["R"]), int(rq["T"]), int(rq["model"])
-        o = {"counts": torch.zeros((1, T + 1, 3), dtype=torch.int64, device=dev),
+        C = fsgp_model_compartments(model)
+        o = {"counts": torch.zeros((1, T + 1, C), dtype=torch.int64, device=dev),
              "steps_run": torch.zeros((1,), dtype=torch.int32, device=dev)}
         if rq.get("freq", True):
-            o["freq"] = torch.zeros((1, 3, g.n), dtype=torch.int32, device=dev)
+            o["freq"] = torch.zeros((1, C, g.n), dtype=torch.int32, device=dev)
         if rq.get("per_real", False):
-            o["per_real"] = torch.zeros((1, R, T + 1, 3), dtype=torch.int32, device=dev)
+            o["per_real"] = torch.zeros((1, R, T + 1, C), dtype=torch.int32, device=dev)
         outs.append(o)
         q = arr[i]
         q.graph = g.handle
         q.model = model
         q.params = fsgp_params(beta=rq.get("beta", 0.0), gamma=rq.get("gamma", 0.0),
-                               ic_mode=rq.get("ic_mode", IC_WEIGHTED_CASCADE), ic_p=rq.get("ic_p", 0.0))
+                               ic_mode=rq.get("ic_mode", IC_WEIGHTED_CASCADE), ic_p=rq.get("ic_p", 0.0),
+                               alpha=rq.get("alpha", 0.0), mu=rq.get("mu", 0.0), nu=rq.get("nu", 0.0))
         q.seed_nodes = seeds.ctypes.data if seeds.size else None
         q.n_seeds = int(seeds.size)
         q.R, q.T, q.rng_seed = R, T, int(rq["rng_seed"])

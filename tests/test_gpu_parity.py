@@ -208,7 +208,7 @@ def test_invalid_arguments_rejected(cuda_lib):
     with pytest.raises(f.FsgpError):
         f.simulate(graph, O.SIR, [np.array([5], np.int32)], 32, 3, 1, beta=1.5, gamma=0.1)
     with pytest.raises(f.FsgpError):
-        f.simulate(graph, 7, [np.array([5], np.int32)], 32, 3, 1)
+        f.simulate(graph, 9, [np.array([5], np.int32)], 32, 3, 1)
     with pytest.raises(f.FsgpError):
         f.simulate(graph, O.SIR, [np.array([5], np.int32)], 32, 3, 1, beta=0.1,
                    options=dict(r_offset=5))
