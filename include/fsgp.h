@@ -147,7 +147,12 @@ typedef struct {
                                graph and launch it at once (ignored when profiling) */
     int32_t lane_words;     /* words per thread of the one-thread-per-row kernel (rows with
                                1..3 in-arcs): 1, 2, 4 or 8 (0 = auto) */
-    int32_t reserved[6];
+    int32_t fuse_rows;      /* 1: every row in one warp-per-row kernel, dense steps only (two
+                               launches per step, for small graphs whose steps are bound by
+                               launch latency; needs in-degree < 65536); -1: never; 0: auto
+                               (graphs of at most 2^20 state words per plane, when no
+                               degree-class or frontier field is set) */
+    int32_t reserved[5];
 } fsgp_options;
 
 /* Caller-owned result buffers, all host or all device (flags).  NULL = not wanted,

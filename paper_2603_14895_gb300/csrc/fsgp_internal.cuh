@@ -97,6 +97,14 @@ struct Workspace {
     size_t bytes = 0;
 };
 
+// An instantiated CUDA graph of one run's step loop, kept for the next run whose launch
+// sequence is the same byte for byte (kernel arguments, grids, output pointers).
+struct ExecCache {
+    std::vector<uint8_t> sig;
+    cudaGraphExec_t exec = nullptr;
+};
+constexpr int kExecCacheSize = 4;
+
 // Per-graph tables of the learned surrogate's aggregation, built on first use: rows with
 // at least kSgLong arcs are split into chunks of kSgChunk arcs whose partial sums meet
 // in a float32 accumulator (zero between uses).
@@ -147,6 +155,7 @@ struct fsgp_graph {
     fsgp::ClassInfo cls{};
     fsgp::HubTable hub{};
     fsgp::Workspace ws{};
+    std::vector<fsgp::ExecCache> execs;   // most recent last (they point into ws)
     fsgp::SgCache sgc{};
     int sm_count = 0;
     size_t device_bytes = 0;
@@ -157,6 +166,8 @@ namespace fsgp {
 // Host helpers shared by the simulation entry points (simulate.cu).
 // Grow the graph's cached workspace to at least `bytes` (contents undefined).
 int ensure_workspace(fsgp_graph *g, size_t bytes);
+// Destroy the graph's cached step-loop executables (they refer to its workspace).
+void drop_exec_cache(fsgp_graph *g);
 // Exact integer survival table surv[k] ~ 2^32 (1 - beta)^k for k = 0 .. min(K_sat,
 // max_deg), where surv[K_sat] = 0 (every lane with k >= K_sat is infected); ksat =
 // INT32_MAX when the table never reaches 0 within max_deg.

@@ -287,6 +287,7 @@ __global__ void k_lane_tab(const int32_t *__restrict__ rp2, const int32_t *__res
 
 static void release(fsgp_graph *g) {
     if (!g) return;
+    drop_exec_cache(g);
     cudaFree(g->row_ptr);
     cudaFree(g->col);
     cudaFree(g->out_ptr);
@@ -536,6 +537,7 @@ extern "C" int fsgp_graph_trim(fsgp_graph *g) {
     cudaGetDevice(&dev);
     cudaSetDevice(g->device);
     cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) drop_exec_cache(g);
     if (e == cudaSuccess && g->ws.ptr) e = cudaFree(g->ws.ptr);
     if (e == cudaSuccess) {
         g->ws.ptr = nullptr;

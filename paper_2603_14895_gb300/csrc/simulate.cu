@@ -392,8 +392,15 @@ static int ensure_hub_table(fsgp_graph *g, int hub_min_deg, int chunk, cudaStrea
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
+void drop_exec_cache(fsgp_graph *g) {
+    for (ExecCache &c : g->execs)
+        if (c.exec) cudaGraphExecDestroy(c.exec);
+    g->execs.clear();
+}
+
 int ensure_workspace(fsgp_graph *g, size_t bytes) {
     if (g->ws.bytes >= bytes) return FSGP_OK;
+    drop_exec_cache(g);
     cudaFree(g->ws.ptr);
     g->ws.ptr = nullptr;
     g->ws.bytes = 0;
@@ -483,9 +490,17 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
         any_init |= sets[i]->init_planes != nullptr;
         want_steps |= sets[i]->steps_run != nullptr;
     }
+    // Small graphs: every row in one warp-per-row launch (16-bit counters), dense steps
+    // only, so that a step is two launches; their steps are bound by launch latency.
+    // (automatic only when no degree-class or frontier option is given)
+    const bool auto_classes = opt.small_max_deg == 0 && opt.hub_min_deg == 0 && opt.hub_chunk == 0 &&
+                              opt.sparse_frac == 0.0;
+    const bool fuse = g->max_deg < 65536 &&
+                      (opt.fuse_rows > 0 ||
+                       (opt.fuse_rows == 0 && auto_classes && (int64_t)n * Wn <= ((int64_t)1 << 20)));
     // degree classes
     int small_max = opt.small_max_deg > 0 ? opt.small_max_deg : 255;
-    int hub_min = opt.hub_min_deg > 0 ? opt.hub_min_deg : 8192;
+    int hub_min = fuse ? 65536 : (opt.hub_min_deg > 0 ? opt.hub_min_deg : 8192);
     int bs = bitlen(small_max + 1) - 1;              // small: d <= 2^bs - 1
     if (bs < 0) bs = 0;
     if (bs > kSmallBits) bs = kSmallBits;             // small rows count on 8-bit slices
@@ -496,7 +511,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     small_max = (1 << bs) - 1;
     hub_min = 1 << (bh - 1);
     const int chunk = opt.hub_chunk > 0 ? std::min(opt.hub_chunk, 65535) : 8192;
-    const double sparse_frac = opt.sparse_frac == 0.0 ? 0.05 : opt.sparse_frac;
+    const double sparse_frac = fuse ? -1.0 : (opt.sparse_frac == 0.0 ? 0.05 : opt.sparse_frac);
     const unsigned long long sparse_limit =
         sparse_frac < 0.0 ? 0ull : (unsigned long long)(sparse_frac * (double)g->nnz);
     const bool allow_sparse = sparse_frac >= 0.0;
@@ -645,19 +660,21 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     Prof prof;
     const bool profiling = opt.profile != nullptr;
     int64_t launches = 0;
-    StepLaunch L{};
+    StepLaunch L;
+    memset(&L, 0, sizeof L);   // padding too: the bytes form the graph-cache signature
     L.V = V;
     L.TEAM = TEAM;
     L.smem_lanes = smem_lanes;
     // the 16..small_max kernel also takes every small row of a frontier step
-    L.have_small = n_small_all > 0;
-    L.have_small4 = n_small4 > 0;
-    L.have_lane = n_lane > 0 || n_d0 > 0;
+    L.have_small = n_small_all > 0 && !fuse;
+    L.have_small4 = n_small4 > 0 && !fuse;
+    L.have_lane = (n_lane > 0 || n_d0 > 0) && !fuse;
     L.swl = occ.swl;
-    L.have_mid = n_mid > 0;
+    L.have_mid = fuse ? n > 0 : n_mid > 0;
     L.have_hub = n_hubs > 0;
     L.prof = profiling ? &prof : nullptr;
-    const int64_t items_small = (int64_t)n_small_all * nslices, items_mid = (int64_t)n_mid * nslices;
+    const int64_t items_small = (int64_t)n_small_all * nslices;
+    const int64_t items_mid = (int64_t)(fuse ? n : n_mid) * nslices;
     const int64_t items_lane = (int64_t)(n_lane + n_d0) * (Wn / occ.swl);
     const int per_block_small = (kBlock / 32) * (32 / TEAM);
     auto grid_for_items = [&](int per_sm, int64_t items) {
@@ -677,7 +694,8 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     const int grid_mark = g->sm_count * 8;
     const int grid_scan = grid_cap((int64_t)n, kBlock, g->sm_count, 8);
 
-    StepArgs A{};
+    StepArgs A;
+    memset(&A, 0, sizeof A);
     A.rp = g->rp2;
     A.col = g->col2;
     A.orig = g->rows_sorted;
@@ -706,8 +724,8 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     A.n_small4 = n_small4;
     A.r_lane = start_lane;
     A.n_lane = n_lane;
-    A.r_mid = start_mid;
-    A.n_mid = n_mid;
+    A.r_mid = fuse ? 0 : start_mid;
+    A.n_mid = fuse ? n : n_mid;
     A.r_d0 = d0_start;
     A.lane_tab = (g->lane_tab && n_lane > 0) ? g->lane_tab + (start_lane - g->lane_start) : nullptr;
     A.d0_list = (int32_t *)(ws + off[O_D0]);
@@ -779,6 +797,32 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     A.t = (uint32_t)opt.t0;
     A.list_in = list[1];
     A.list_out = list[0];
+    // The step loop's kernels and their arguments follow from these values (the
+    // workspace and output pointers included): a run with the same signature reuses the
+    // executable graph captured by an earlier run instead of capturing a new one.
+    std::vector<uint8_t> sig;
+    int cached = -1;
+    if (capture) {
+        auto put = [&sig](const void *p, size_t b) {
+            sig.insert(sig.end(), (const uint8_t *)p, (const uint8_t *)p + b);
+        };
+        const int flags[6] = {model, T, allow_sparse ? 1 : 0, any_init ? 1 : 0, want_lanes ? 1 : 0,
+                              want_freq ? 1 : 0};
+        put(flags, sizeof flags);
+        put(&sparse_limit, sizeof sparse_limit);
+        put(&A, sizeof A);
+        put(&L, sizeof L);
+        put(&d_out, sizeof d_out);
+        for (int i = 0; i < S; ++i) {
+            put(&ho[i].planes, sizeof ho[i].planes);
+            put(&hp[i].W, sizeof hp[i].W);
+        }
+        for (size_t c = 0; c < g->execs.size(); ++c)
+            if (g->execs[c].sig == sig) cached = (int)c;
+    }
+    if (cached >= 0) {
+        FSGP_CUDA(cudaGraphLaunch(g->execs[(size_t)cached].exec, s));
+    } else {
     if (capture) FSGP_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     k_init_scan<<<grid_scan, kBlock, smem_lanes, s>>>(A, model);
     ++launches;
@@ -833,8 +877,16 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
         e = cudaGraphLaunch(exec, s);
-        cudaGraphExecDestroy(exec);   // freed once the launch completes
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+        if (e != cudaSuccess) {
+            cudaGraphExecDestroy(exec);
+            return cuda_fail(e, "cudaGraphLaunch");
+        }
+        if ((int)g->execs.size() >= kExecCacheSize) {
+            cudaGraphExecDestroy(g->execs.front().exec);   // released once its launches complete
+            g->execs.erase(g->execs.begin());
+        }
+        g->execs.push_back(ExecCache{std::move(sig), exec});
+    }
     }
     FSGP_CUDA(cudaGetLastError());
 

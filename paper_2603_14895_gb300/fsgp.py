@@ -56,7 +56,8 @@ class fsgp_options(ctypes.Structure):
                 ("sparse_frac", ctypes.c_double), ("r_offset", ctypes.c_int32),
                 ("t0", ctypes.c_int32), ("init_planes", ctypes.c_void_p),
                 ("profile", ctypes.POINTER(fsgp_profile)), ("capture_graph", ctypes.c_int32),
-                ("lane_words", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("lane_words", ctypes.c_int32), ("fuse_rows", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class fsgp_result(ctypes.Structure):
