@@ -57,7 +57,8 @@ extern "C" {
 #define FSGP_EINVAL (-1)          /* an argument is out of range or inconsistent */
 #define FSGP_ENOMEM (-2)          /* device or host allocation failed */
 #define FSGP_ECUDA (-3)           /* a CUDA runtime call failed (message has details) */
-/* (-4) is not used: no kernel of this library waits on another CTA or device */
+#define FSGP_ETIMEOUT (-4)        /* a bounded device-side wait ran out (the surrogate's
+                                     tensor-core completion wait) */
 #define FSGP_EUNSUPPORTED (-5)    /* a valid request this library version does not implement */
 
 /* ------------------------------------------------------------------------ models */

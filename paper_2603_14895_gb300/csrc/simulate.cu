@@ -436,6 +436,8 @@ static int occupancy_model(int model, int V, int TEAM, size_t smem, RowOccupancy
     }
 }
 
+constexpr int32_t kSmallMaxFused = 255;   // in-degree bound of the 8-bit team kernel
+
 static int words_per_set(int R) {
     const int W = (R + 31) / 32;
     int Ws = 1;
@@ -470,7 +472,17 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     const int C = n_compartments(model);
     const int Wn = S * Ws;
     const int pd = Ws << __builtin_ctz((unsigned)S);   // largest power of two dividing Wn
-    int V = opt.vector_words ? opt.vector_words : 2;   // 2 measured best on GB300
+    // Small graphs: every row in one launch (team or warp per row), dense steps
+    // only, so that a step is two launches; their steps are bound by launch latency.
+    // (automatic only when no degree-class or frontier option is given)
+    const bool auto_classes = opt.small_max_deg == 0 && opt.hub_min_deg == 0 && opt.hub_chunk == 0 &&
+                              opt.sparse_frac == 0.0;
+    const bool fuse = g->max_deg < 65536 &&
+                      (opt.fuse_rows > 0 ||
+                       (opt.fuse_rows == 0 && auto_classes && (int64_t)n * Wn <= ((int64_t)1 << 20)));
+    // Words per thread: 2 measured best on GB300 for large graphs; small graphs, bound by
+    // the longest per-thread chain of dependent instructions, take one word per thread.
+    int V = opt.vector_words ? opt.vector_words : (fuse ? 1 : 2);
     if (V != 1 && V != 2 && V != 4) return fail(FSGP_EINVAL, "vector_words must be 1, 2 or 4");
     if (V > pd) V = pd;
     const int SW = std::min(32 * V, pd);
@@ -490,14 +502,6 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
         any_init |= sets[i]->init_planes != nullptr;
         want_steps |= sets[i]->steps_run != nullptr;
     }
-    // Small graphs: every row in one warp-per-row launch (16-bit counters), dense steps
-    // only, so that a step is two launches; their steps are bound by launch latency.
-    // (automatic only when no degree-class or frontier option is given)
-    const bool auto_classes = opt.small_max_deg == 0 && opt.hub_min_deg == 0 && opt.hub_chunk == 0 &&
-                              opt.sparse_frac == 0.0;
-    const bool fuse = g->max_deg < 65536 &&
-                      (opt.fuse_rows > 0 ||
-                       (opt.fuse_rows == 0 && auto_classes && (int64_t)n * Wn <= ((int64_t)1 << 20)));
     // degree classes
     int small_max = opt.small_max_deg > 0 ? opt.small_max_deg : 255;
     int hub_min = fuse ? 65536 : (opt.hub_min_deg > 0 ? opt.hub_min_deg : 8192);
@@ -666,14 +670,17 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     L.TEAM = TEAM;
     L.smem_lanes = smem_lanes;
     // the 16..small_max kernel also takes every small row of a frontier step
-    L.have_small = n_small_all > 0 && !fuse;
+    // fused rows: the team-per-row kernel (8-bit counters) when every in-degree is below
+    // 256, else the warp-per-row kernel (16-bit counters)
+    const bool fuse_team = fuse && g->max_deg <= kSmallMaxFused;
+    L.have_small = fuse ? (fuse_team && n > 0) : n_small_all > 0;
     L.have_small4 = n_small4 > 0 && !fuse;
     L.have_lane = (n_lane > 0 || n_d0 > 0) && !fuse;
     L.swl = occ.swl;
-    L.have_mid = fuse ? n > 0 : n_mid > 0;
+    L.have_mid = fuse ? (!fuse_team && n > 0) : n_mid > 0;
     L.have_hub = n_hubs > 0;
     L.prof = profiling ? &prof : nullptr;
-    const int64_t items_small = (int64_t)n_small_all * nslices;
+    const int64_t items_small = (int64_t)(fuse_team ? n : n_small_all) * nslices;
     const int64_t items_mid = (int64_t)(fuse ? n : n_mid) * nslices;
     const int64_t items_lane = (int64_t)(n_lane + n_d0) * (Wn / occ.swl);
     const int per_block_small = (kBlock / 32) * (32 / TEAM);
@@ -718,8 +725,8 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     A.ctl = ctl;
     A.lane_cnt = want_lanes ? (int32_t *)(ws + off[O_LANES]) : nullptr;
     A.np = P;
-    A.r_small = start_small;
-    A.n_small = n_small;
+    A.r_small = fuse_team ? 0 : start_small;
+    A.n_small = fuse_team ? n : n_small;
     A.r_small4 = std::max(start_small4, start_small);
     A.n_small4 = n_small4;
     A.r_lane = start_lane;

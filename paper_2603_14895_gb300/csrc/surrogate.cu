@@ -10,8 +10,10 @@
 //   h'_v = ReLU(h_v Ws_l + m_v Wn_l + b_l), l = 1..3, width 64
 //   p_v  = sigmoid(h3_v . w_o + b_o),  loss = mean_v (p_v - y_v)^2
 //
-// Dense products run on the tensor cores (mma.sync m16n8k16, bfloat16 operands, float32
-// accumulation); activations are stored as bfloat16, gradients and the Adam state in
+// The forward dense layers run on the fifth-generation tensor cores (tcgen05.mma into
+// tensor memory, bfloat16 operands, float32 accumulation; the last layer applies the
+// output head in its epilogue); the backward products use mma.sync m16n8k16 on the same
+// operand types.  Activations are stored as bfloat16, gradients and the Adam state in
 // float32.  Every kernel is this project's own.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -99,43 +101,72 @@ __global__ void k_seed_bits(const int32_t *__restrict__ cand, int32_t k, int32_t
     if (advance && threadIdx.x == 0) *cur = c + 1;
 }
 
-// m_v = mean over in-arcs of h_u (bfloat16 in and out, float32 sums).  F/2 threads per
-// work item, one bfloat16 pair each.  Items 0..n-1 are rows (rows with >= kSgLong arcs
-// are skipped); items n.. are the chunks of those long rows, whose partial sums go to
-// acc[slot] for k_agg_fin.
+// m_v = mean over in-arcs of h_u (bfloat16 in and out, float32 sums).  A group of
+// G = agg_arcs<F>() * F/8 threads takes one work item: F/8 threads cover the F features
+// of a source row (16 bytes each) and the subgroups take every agg_arcs-th arc, so each
+// load instruction fetches several source rows; the subgroups' sums meet by shuffle.
+// (Measured on GB300, BA n = 500k: two subgroups for F = 64, four for F = 8.)
+// Items 0..n-1 are rows (rows with >= kSgLong arcs are skipped); items n.. are the chunks
+// of those long rows, whose partial sums go to acc[slot] for k_agg_fin.
+template <int F>
+__host__ __device__ constexpr int agg_arcs() { return F == 8 ? 4 : 2; }
 template <int F>
 __global__ void k_agg(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int32_t n,
                       const bf16 *__restrict__ h, bf16 *m, const int4 *__restrict__ items, int32_t n_items,
                       float *acc) {
-    constexpr int TPR = F / 2;
+    constexpr int TPR = F / 8;
+    constexpr int kAggArcs = agg_arcs<F>();
+    constexpr int G = TPR * kAggArcs;
+    static_assert(G <= 32 && (32 % G) == 0, "a group lies within a warp");
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-    const int j = (int)(t % TPR);
+    const int j = (int)(t % TPR);                // 16-byte feature chunk
+    const int sub = (int)((t / TPR) % kAggArcs); // arc subgroup
     const int64_t total = (int64_t)n + n_items;
-    for (int64_t v = t / TPR; v < total; v += nthreads / TPR) {
-        int32_t row, b, e, slot = -1;
-        if (v < n) {
-            row = (int32_t)v;
-            b = row_ptr[v];
-            e = row_ptr[v + 1];
-            if (e - b >= kSgLong) continue;
-        } else {
-            const int4 it = items[v - n];
-            row = it.x, b = it.y, e = it.z, slot = it.w;
+    // whole warps iterate together (the shuffles below need every lane of the group)
+    const int64_t v_end = (total + (nthreads / G) - 1) / (nthreads / G) * (nthreads / G);
+    for (int64_t v = t / G; v < v_end; v += nthreads / G) {
+        int32_t row = 0, b = 0, e = 0, slot = -1;
+        bool skip = v >= total;
+        if (!skip) {
+            if (v < n) {
+                row = (int32_t)v;
+                b = row_ptr[v];
+                e = row_ptr[v + 1];
+                if (e - b >= kSgLong) skip = true;
+            } else {
+                const int4 it = items[v - n];
+                row = it.x, b = it.y, e = it.z, slot = it.w;
+            }
         }
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll 4
-        for (int32_t a = b; a < e; ++a) {
-            const bf162 x = reinterpret_cast<const bf162 *>(h + (size_t)__ldg(col + a) * F)[j];
-            s0 += __bfloat162float(x.x);
-            s1 += __bfloat162float(x.y);
+        float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (!skip) {
+#pragma unroll 2
+            for (int32_t a = b + sub; a < e; a += kAggArcs) {
+                const uint4 x = __ldg(reinterpret_cast<const uint4 *>(h + (size_t)__ldg(col + a) * F) + j);
+                const bf162 *xp = reinterpret_cast<const bf162 *>(&x);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    sum[2 * i] += __bfloat162float(xp[i].x);
+                    sum[2 * i + 1] += __bfloat162float(xp[i].y);
+                }
+            }
         }
+#pragma unroll
+        for (int o = TPR; o < G; o <<= 1)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) sum[i] += __shfl_xor_sync(0xffffffffu, sum[i], o);
+        if (skip || sub != 0) continue;
         if (slot < 0) {
             const float inv = e > b ? 1.f / (float)(e - b) : 0.f;
-            reinterpret_cast<bf162 *>(m + (size_t)row * F)[j] = __floats2bfloat162_rn(s0 * inv, s1 * inv);
+            uint4 o;
+            bf162 *op = reinterpret_cast<bf162 *>(&o);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) op[i] = __floats2bfloat162_rn(sum[2 * i] * inv, sum[2 * i + 1] * inv);
+            reinterpret_cast<uint4 *>(m + (size_t)row * F)[j] = o;
         } else {
-            atomicAdd(acc + (size_t)slot * F + 2 * j, s0);
-            atomicAdd(acc + (size_t)slot * F + 2 * j + 1, s1);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) atomicAdd(acc + (size_t)slot * F + 8 * j + i, sum[i]);
         }
     }
 }
@@ -166,83 +197,201 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// y = ReLU([h | m] W + b) for a row tile: one warp per 16 rows x 64 columns, K = 2F.
-// W (K x 64, rows of Ws then Wn) is staged transposed in shared memory.
-template <int F>
-__global__ void __launch_bounds__(128) k_dense(const bf16 *__restrict__ h, const bf16 *__restrict__ m,
-                                               const bf16 *__restrict__ Ws, const bf16 *__restrict__ Wn,
-                                               const float *__restrict__ bias, int32_t n, bf16 *y) {
-    constexpr int K = 2 * F;
-    constexpr int KP = K + 8;   // padded row (bank spread)
-    __shared__ __align__(16) bf16 Wt[H * KP];
-    for (int i = threadIdx.x; i < K * H; i += blockDim.x) {
-        const int k = i / H, c = i % H;
-        Wt[c * KP + k] = k < F ? Ws[k * H + c] : Wn[(k - F) * H + c];
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, tg = lane & 3;
-    const int64_t tiles = ((int64_t)n + 15) / 16;
-    for (int64_t tile = (int64_t)blockIdx.x * 4 + warp; tile < tiles; tile += (int64_t)gridDim.x * 4) {
-        const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
-        float acc[8][4];
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-#pragma unroll
-        for (int ks = 0; ks < K / 16; ++ks) {
-            const int k0 = ks * 16;
-            // A fragment: columns k0 + 2tg (+1) and k0 + 8 + 2tg (+1) of rows r0, r1
-            uint32_t a[4];
-            const int ca = k0 + 2 * tg, cb = k0 + 8 + 2 * tg;
-            auto col_ptr = [&](int64_t r, int c) -> const bf16 * {
-                return c < F ? h + (size_t)r * F + c : m + (size_t)r * F + (c - F);
-            };
-            a[0] = r0 < n ? ld_b32(col_ptr(r0, ca)) : 0u;
-            a[1] = r1 < n ? ld_b32(col_ptr(r1, ca)) : 0u;
-            a[2] = r0 < n ? ld_b32(col_ptr(r0, cb)) : 0u;
-            a[3] = r1 < n ? ld_b32(col_ptr(r1, cb)) : 0u;
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const bf16 *wr = Wt + (nt * 8 + g) * KP;
-                const uint32_t b0 = ld_b32(wr + k0 + 2 * tg);
-                const uint32_t b1 = ld_b32(wr + k0 + 8 + 2 * tg);
-                mma_bf16(acc[nt], a, b0, b1);
-            }
-        }
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const int c = nt * 8 + 2 * tg;
-            const float bb0 = bias[c], bb1 = bias[c + 1];
-            if (r0 < n)
-                *reinterpret_cast<bf162 *>(y + (size_t)r0 * H + c) =
-                    __floats2bfloat162_rn(fmaxf(acc[nt][0] + bb0, 0.f), fmaxf(acc[nt][1] + bb1, 0.f));
-            if (r1 < n)
-                *reinterpret_cast<bf162 *>(y + (size_t)r1 * H + c) =
-                    __floats2bfloat162_rn(fmaxf(acc[nt][2] + bb0, 0.f), fmaxf(acc[nt][3] + bb1, 0.f));
-        }
-    }
+// ------------------------------------------------------- dense layer on tcgen05 / TMEM
+//
+// y = ReLU([h | m] W + b) for tiles of 128 rows, K = 2F (16 or 128), N = 64, on the
+// fifth-generation tensor cores: both operands staged in shared memory in the canonical
+// K-major layout without swizzle (8-row x 16-byte core matrices; the two K-neighbour core
+// matrices of one instruction lie 128 B apart, 8-row groups K*16 B apart), one elected
+// thread issues K/16 tcgen05.mma (kind::f16: bfloat16 in, float32 accumulate) into a
+// 128-lane x 64-column tensor-memory accumulator, commits them to an mbarrier, and the
+// four warps read their 32 lanes back (tcgen05.ld) for bias, ReLU and the bfloat16 store.
+// Persistent CTAs loop over tiles; W^T is staged once per CTA.
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start address, leading (K) and stride (8-row group)
+// byte offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 
-// p_v = sigmoid(h3 . wo + bo); optional sum of p into *psum (screening score).
-__global__ void k_head(const bf16 *__restrict__ h3, const bf16 *__restrict__ wo, const float *__restrict__ bo,
-                       int32_t n, float *p, float *psum, const int32_t *cur) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const bf162 w = reinterpret_cast<const bf162 *>(wo)[lane];
-    float local = 0.f;
-    for (int64_t v = warp; v < n; v += nw) {
-        const bf162 x = reinterpret_cast<const bf162 *>(h3 + (size_t)v * H)[lane];
-        float s = __bfloat162float(x.x) * __bfloat162float(w.x) + __bfloat162float(x.y) * __bfloat162float(w.y);
+// Byte offset of the 16-byte chunk kc of row r in a K-major core-matrix tile of KC chunks.
+__device__ __forceinline__ uint32_t core_off(int r, int kc, int KC) {
+    return (uint32_t)(((r >> 3) * KC + kc) * 128 + (r & 7) * 16);
+}
+
+constexpr int kTcRows = 128;            // rows per tile (MMA M)
+constexpr int kTcWaitLimit = 1 << 24;   // mbarrier polls before giving up
+
+// Two A tiles (the next one is fetched with cp.async while the current one is multiplied)
+// and W^T.
+template <int F>
+constexpr size_t tc_smem_bytes() { return (size_t)(2 * kTcRows + H) * (2 * F) * 2; }
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
+    // a source size of 0 fills the 16 bytes with zeros (rows past the end)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0));
+}
+
+// HEAD: the epilogue also applies the output head, p = sigmoid(h . w_o + b_o) of the
+// bfloat16 layer output, and writes p (when p_out is set) and / or adds the sum of p
+// into psum[*cur] (screening); y (the layer output) may then be null.
+template <int F, bool HEAD>
+__global__ void __launch_bounds__(128) k_dense_tc(const bf16 *__restrict__ h, const bf16 *__restrict__ m,
+                                                  const bf16 *__restrict__ Ws, const bf16 *__restrict__ Wn,
+                                                  const float *__restrict__ bias, int32_t n, bf16 *y,
+                                                  const bf16 *__restrict__ wo, const float *__restrict__ bo,
+                                                  float *p_out, float *psum, const int32_t *cur, int32_t *err) {
+    constexpr int K = 2 * F;
+    constexpr int KC = K / 8;            // 16-byte chunks per row
+    constexpr int TILE = kTcRows * K * 2;
+    extern __shared__ __align__(1024) uint8_t tc_smem[];
+    uint8_t *sA0 = tc_smem;                         // 2 x (128 x K)
+    uint8_t *sB = tc_smem + 2 * TILE;               // 64 x K (W transposed)
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t tiles = ((int64_t)n + kTcRows - 1) / kTcRows;
+    if ((int64_t)blockIdx.x >= tiles) return;
+    auto stage = [&](int buf, int64_t tile) {
+        const uint32_t base = smem_addr(sA0 + buf * TILE);
+        const int64_t row0 = tile * kTcRows;
+        for (int c = tid; c < kTcRows * KC; c += blockDim.x) {
+            const int r = c / KC, kc = c % KC;
+            const int64_t row = row0 + r;
+            const bool valid = row < n;
+            const int64_t rr = valid ? row : 0;
+            const bf16 *src = kc < KC / 2 ? h + (size_t)rr * F + kc * 8 : m + (size_t)rr * F + (kc - KC / 2) * 8;
+            cp_async16(base + core_off(r, kc, KC), src, valid);
+        }
+        asm volatile("cp.async.commit_group;");
+    };
+    stage(0, blockIdx.x);
+    // B: output column c holds its K inputs, Ws rows then Wn rows (coalesced row reads,
+    // element-wise transposed stores)
+    for (int i = tid; i < K * H; i += blockDim.x) {
+        const int k = i / H, col = i % H;
+        const bf16 w = k < F ? Ws[k * H + col] : Wn[(k - F) * H + col];
+        *reinterpret_cast<bf16 *>(sB + core_off(col, k >> 3, KC) + (k & 7) * 2) = w;
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_addr(&tmem_base)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // kind::f16: D f32 (bit 4), A and B bf16 (bits 7, 10), K-major, N = 64, M = 128
+    constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(H >> 3) << 17) |
+                               ((uint32_t)(kTcRows >> 4) << 24);
+    float wo_f[HEAD ? H : 1];
+    float bo_f = 0.f;
+    if constexpr (HEAD) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        const float pv = 1.f / (1.f + expf(-(s + bo[0])));
-        if (lane == 0) {
-            if (p) p[v] = pv;
-            local += pv;
+        for (int j = 0; j < H; ++j) wo_f[j] = __bfloat162float(wo[j]);
+        bo_f = bo[0];
+    }
+    float psum_local = 0.f;
+    uint32_t phase = 0;
+    bool ok = true;
+    int buf = 0;
+    for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, buf ^= 1) {
+        const int64_t next = tile + gridDim.x;
+        if (next < tiles) {
+            stage(buf ^ 1, next);
+            asm volatile("cp.async.wait_group 1;");   // this tile's copies are done
+        } else {
+            asm volatile("cp.async.wait_group 0;");
+        }
+        asm volatile("fence.proxy.async.shared::cta;");   // smem writes -> tensor-core reads
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t tbase = tmem_base;
+        if (tid == 0) {
+            const uint32_t a0 = smem_addr(sA0 + buf * TILE), b0 = smem_addr(sB);
+#pragma unroll
+            for (int k = 0; k < K / 16; ++k) {
+                const uint64_t ad = umma_desc(a0 + k * 256, 128, KC * 128);
+                const uint64_t bd = umma_desc(b0 + k * 256, 128, KC * 128);
+                const uint32_t accum = k > 0 ? 1u : 0u;
+                asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                             ::"r"(tbase), "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(smem_addr(&mbar)));
+        }
+        uint32_t done = 0;
+        for (int it = 0; it < kTcWaitLimit && !done; ++it)
+            asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                         " selp.u32 %0, 1, 0, p;\n}"
+                         : "=r"(done) : "r"(smem_addr(&mbar)), "r"(phase));
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!done) {
+            ok = false;
+            atomicExch(err, 1);
+            // give the issued MMAs a second bounded wait before the TMEM is freed
+            for (int it = 0; it < kTcWaitLimit && !done; ++it)
+                asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                             " selp.u32 %0, 1, 0, p;\n}"
+                             : "=r"(done) : "r"(smem_addr(&mbar)), "r"(phase ^ 1u));
+        } else {
+            const int64_t row = tile * kTcRows + 32 * warp + lane;   // this thread's lane
+            float dot = 0.f;
+#pragma unroll
+            for (int c0 = 0; c0 < H; c0 += 16) {
+                uint32_t r[16];
+                const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+                               "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                             : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                bf162 o[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    o[j] = __floats2bfloat162_rn(fmaxf(__uint_as_float(r[2 * j]) + bias[c0 + 2 * j], 0.f),
+                                                 fmaxf(__uint_as_float(r[2 * j + 1]) + bias[c0 + 2 * j + 1], 0.f));
+                if constexpr (HEAD) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        dot += __bfloat162float(o[j].x) * wo_f[c0 + 2 * j] + __bfloat162float(o[j].y) * wo_f[c0 + 2 * j + 1];
+                }
+                if (y && row < n) {
+                    uint4 *dst = reinterpret_cast<uint4 *>(y + (size_t)row * H + c0);
+                    dst[0] = *reinterpret_cast<const uint4 *>(&o[0]);
+                    dst[1] = *reinterpret_cast<const uint4 *>(&o[4]);
+                }
+            }
+            if constexpr (HEAD) {
+                if (row < n) {
+                    const float pv = 1.f / (1.f + expf(-(dot + bo_f)));
+                    if (p_out) p_out[row] = pv;
+                    psum_local += pv;
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        ok = __syncthreads_and(ok) != 0;   // also orders this tile's reads before the next tile
+        asm volatile("tcgen05.fence::after_thread_sync;");
+    }
+    asm volatile("cp.async.wait_group 0;");
+    if constexpr (HEAD) {
+        if (psum) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) psum_local += __shfl_xor_sync(0xffffffffu, psum_local, o);
+            if (lane == 0 && psum_local != 0.f) atomicAdd(psum + *cur, psum_local);
         }
     }
-    if (psum && lane == 0 && local != 0.f) atomicAdd(psum + *cur, local);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem_base));
 }
 
 // ----------------------------------------------------------------- backward kernels
@@ -539,6 +688,7 @@ struct fsgp_surrogate {
     double *loss = nullptr;
     int32_t *cur = nullptr;
     int32_t *cnt = nullptr;     // seed in-arc counts per node (kept at zero between calls)
+    int32_t *tc_err = nullptr;  // set by a dense-layer CTA whose tensor-core wait ran out
 };
 
 namespace {
@@ -576,6 +726,21 @@ int sg_ensure(fsgp_surrogate *s, int64_t n) {
         return cuda_fail(e, "cudaMalloc (surrogate activations)");
     }
     s->cap = n;
+    return FSGP_OK;
+}
+
+// Persistent CTAs of the tensor-core dense layer: two per SM at most, one per tile at least.
+int tc_grid(const fsgp_surrogate *s, int64_t n) {
+    const int64_t tiles = (n + kTcRows - 1) / kTcRows;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)s->sm_count * 2));
+}
+
+// A tensor-core wait of an earlier launch ran out (the flag is sticky): FSGP_ETIMEOUT.
+int sg_check_tc(fsgp_surrogate *s, cudaStream_t st) {
+    int32_t h = 0;
+    FSGP_CUDA(cudaMemcpyAsync(&h, s->tc_err, sizeof h, cudaMemcpyDeviceToHost, st));
+    FSGP_CUDA(cudaStreamSynchronize(st));
+    if (h) return fail(FSGP_ETIMEOUT, "a tensor-core completion wait of the surrogate's dense layer ran out");
     return FSGP_OK;
 }
 
@@ -656,28 +821,32 @@ void sg_forward(fsgp_surrogate *s, const fsgp_graph *g, float *p, float *psum, c
     const float *B = s->theta;
     const SgCache &C = g->sgc;
     const int64_t items = (int64_t)n + C.n_in_items;
-    k_agg<F0><<<grid_of(s, items * (F0 / 2), 256), 256, 0, st>>>(g->row_ptr, g->col, n, s->x, s->m1, C.in_items,
+    k_agg<F0><<<grid_of(s, items * (F0 / 8) * agg_arcs<F0>(), 256), 256, 0, st>>>(g->row_ptr, g->col, n, s->x, s->m1, C.in_items,
                                                                  C.n_in_items, C.acc);
     if (C.n_in_long)
         k_agg_fin<F0><<<grid_of(s, (int64_t)C.n_in_long * (F0 / 2), 256), 256, 0, st>>>(C.in_long, C.n_in_long,
                                                                                      g->row_ptr, C.acc, s->m1);
-    k_dense<F0><<<grid_of(s, ((int64_t)n + 63) / 64 * 128, 128, 16), 128, 0, st>>>(
-        s->x, s->m1, W + OFF_WS1, W + OFF_WN1, B + OFF_B1, n, s->h1);
-    k_agg<H><<<grid_of(s, items * (H / 2), 256), 256, 0, st>>>(g->row_ptr, g->col, n, s->h1, s->m2, C.in_items,
+    k_dense_tc<F0, false><<<tc_grid(s, n), 128, tc_smem_bytes<F0>(), st>>>(
+        s->x, s->m1, W + OFF_WS1, W + OFF_WN1, B + OFF_B1, n, s->h1, nullptr, nullptr, nullptr, nullptr, nullptr,
+        s->tc_err);
+    k_agg<H><<<grid_of(s, items * (H / 8) * agg_arcs<H>(), 256), 256, 0, st>>>(g->row_ptr, g->col, n, s->h1, s->m2, C.in_items,
                                                               C.n_in_items, C.acc);
     if (C.n_in_long)
         k_agg_fin<H><<<grid_of(s, (int64_t)C.n_in_long * (H / 2), 256), 256, 0, st>>>(C.in_long, C.n_in_long,
                                                                                    g->row_ptr, C.acc, s->m2);
-    k_dense<H><<<grid_of(s, ((int64_t)n + 63) / 64 * 128, 128, 16), 128, 0, st>>>(
-        s->h1, s->m2, W + OFF_WS2, W + OFF_WN2, B + OFF_B2, n, s->h2);
-    k_agg<H><<<grid_of(s, items * (H / 2), 256), 256, 0, st>>>(g->row_ptr, g->col, n, s->h2, s->m3, C.in_items,
+    k_dense_tc<H, false><<<tc_grid(s, n), 128, tc_smem_bytes<H>(), st>>>(
+        s->h1, s->m2, W + OFF_WS2, W + OFF_WN2, B + OFF_B2, n, s->h2, nullptr, nullptr, nullptr, nullptr, nullptr,
+        s->tc_err);
+    k_agg<H><<<grid_of(s, items * (H / 8) * agg_arcs<H>(), 256), 256, 0, st>>>(g->row_ptr, g->col, n, s->h2, s->m3, C.in_items,
                                                               C.n_in_items, C.acc);
     if (C.n_in_long)
         k_agg_fin<H><<<grid_of(s, (int64_t)C.n_in_long * (H / 2), 256), 256, 0, st>>>(C.in_long, C.n_in_long,
                                                                                    g->row_ptr, C.acc, s->m3);
-    k_dense<H><<<grid_of(s, ((int64_t)n + 63) / 64 * 128, 128, 16), 128, 0, st>>>(
-        s->h2, s->m3, W + OFF_WS3, W + OFF_WN3, B + OFF_B3, n, s->h3);
-    k_head<<<grid_of(s, (int64_t)n * 32, 256), 256, 0, st>>>(s->h3, W + OFF_WO, B + OFF_BO, n, p, psum, s->cur);
+    // layer 3 with the head in its epilogue; h3 is kept only when p is (the backward
+    // pass reads both)
+    k_dense_tc<H, true><<<tc_grid(s, n), 128, tc_smem_bytes<H>(), st>>>(
+        s->h2, s->m3, W + OFF_WS3, W + OFF_WN3, B + OFF_B3, n, p ? s->h3 : nullptr, W + OFF_WO, B + OFF_BO, p, psum,
+        s->cur, s->tc_err);
 }
 
 int sg_prepare_inputs(fsgp_surrogate *s, const fsgp_graph *g, const int32_t *seeds_host, int64_t ns,
@@ -761,7 +930,15 @@ extern "C" int fsgp_surrogate_create(uint64_t init_seed, fsgp_surrogate **out) {
         (e = cudaMalloc(&s->grad, sizeof(float) * N_PARAMS)) != cudaSuccess ||
         (e = cudaMalloc(&s->wb, sizeof(bf16) * N_PARAMS)) != cudaSuccess ||
         (e = cudaMalloc(&s->loss, sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&s->cur, sizeof(int32_t))) != cudaSuccess) {
+        (e = cudaMalloc(&s->cur, sizeof(int32_t))) != cudaSuccess ||
+        (e = cudaMalloc(&s->tc_err, sizeof(int32_t))) != cudaSuccess ||
+        (e = cudaMemset(s->tc_err, 0, sizeof(int32_t))) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_dense_tc<F0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tc_smem_bytes<F0>())) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_dense_tc<H, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tc_smem_bytes<H>())) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_dense_tc<H, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tc_smem_bytes<H>())) != cudaSuccess) {
         fsgp_surrogate_destroy(s);
         return cuda_fail(e, "cudaMalloc (surrogate)");
     }
@@ -809,6 +986,7 @@ extern "C" int fsgp_surrogate_destroy(fsgp_surrogate *s) {
     cudaFree(s->wb);
     cudaFree(s->loss);
     cudaFree(s->cur);
+    cudaFree(s->tc_err);
     delete s;
     return FSGP_OK;
 }
@@ -854,8 +1032,7 @@ extern "C" int fsgp_surrogate_grad(fsgp_surrogate *s, const fsgp_graph *g, const
     if (rc) return rc;
     if (loss_out) FSGP_CUDA(cudaMemcpyAsync(loss_out, s->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
     if (grad_out) FSGP_CUDA(cudaMemcpyAsync(grad_out, s->grad, sizeof(float) * N_PARAMS, cudaMemcpyDeviceToHost, st));
-    FSGP_CUDA(cudaStreamSynchronize(st));
-    return FSGP_OK;
+    return sg_check_tc(s, st);
 }
 
 extern "C" int fsgp_surrogate_train_step(fsgp_surrogate *s, const fsgp_graph *g, const int32_t *seeds_host,
@@ -949,6 +1126,7 @@ extern "C" int fsgp_surrogate_screen(fsgp_surrogate *s, const fsgp_graph *g, con
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         cudaGraphExecDestroy(exec);
         if (e != cudaSuccess) rc = cuda_fail(e, "screen");
+        else rc = sg_check_tc(s, st);
     } while (0);
     cudaFree(d_cand);
     cudaFree(d_scores);

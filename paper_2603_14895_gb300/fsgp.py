@@ -18,7 +18,7 @@ _lock = threading.Lock()
 _lib = None
 
 FSGP_OK = 0
-FSGP_EINVAL, FSGP_ENOMEM, FSGP_ECUDA, FSGP_EUNSUPPORTED = -1, -2, -3, -5
+FSGP_EINVAL, FSGP_ENOMEM, FSGP_ECUDA, FSGP_ETIMEOUT, FSGP_EUNSUPPORTED = -1, -2, -3, -4, -5
 SIR, SIS, IC, LT = 0, 1, 2, 3
 SI, SEIR, SEIS, SWIR = 4, 5, 6, 7
 PTR_HOST, PTR_DEVICE = 0, 1
