@@ -146,18 +146,19 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kind: str):
-    """DRAM bytes per launch of a kernel kind from the committed ncu summary, or None
+def ncu_traffic_ratios():
+    """DRAM bytes over algorithmic bytes per kernel kind and model, from the committed
+    summary of small ncu captures (one kernel, one mid-run step, R-MAT scale 23), or None
     if absent or taken on different kernel sources."""
-    p = os.path.join(ROOT, "profiles", "traffic_rmat26.json")
+    p = os.path.join(ROOT, "profiles", "traffic_step_rmat23.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     if d.get("source_hash") != kernel_source_hash():
         return None
-    k = d.get("kernels", {}).get(kind)
-    return None if k is None else float(k["dram_bytes_per_launch"])
+    return {m: {k: float(v["dram_over_alg"]) for k, v in kinds.items()}
+            for m, kinds in d.get("models", {}).items()}
 
 
 def build_workload(scale: int):
@@ -356,17 +357,135 @@ def run_config_bench(args, which: str):
             "clocks": clocks}
 
 
+def step_bytes(n: int, nnz: int, R: int, planes: int) -> float:
+    """Algorithmic bytes of one dense propagation step (every node updated from all its
+    in-arcs, Sec. 2 Eq. nodestate over Sec. 3.1 Eq. agg): column indices 4E, row pointers
+    4(N+1), one 32-byte sector (or the node's whole word run, if larger) per gathered
+    source, and the node's own P state planes read and written."""
+    ws = 1
+    while ws * 32 < R:
+        ws *= 2
+    w = 4 * ws
+    return 4.0 * nnz + 4.0 * (n + 1) + float(nnz) * max(32, w) + 2.0 * planes * n * w
+
+
+def run_step_bench(args):
+    """One mid-run dense step of SIR and of SIS on the R-MAT graph of --scale (R = 256,
+    beta = 0.01, gamma = 0.05, the benchmark's seeds): the state after --t-mid steps is
+    exported, and one step from it is timed per kernel kind over --steps repetitions.
+    Each model's step also runs once inside the NVTX range "fsgp_step_<model>", with no
+    profiling events, for an ncu capture of exactly that step's launches."""
+    import torch
+    from paper_2603_14895_gb300 import fsgp
+    torch.cuda.set_device(0)
+    g, seeds = build_workload(args.scale)
+    graph = fsgp.Graph(g.row_ptr, g.col_idx)
+    kinds = fsgp.PROFILE_KINDS
+    peak, peak_kind = measured_peaks()
+    res = {}
+    for m, nm in zip(MODELS, ("SIR", "SIS")):
+        o = fsgp.simulate(graph, m, [seeds], R, args.t_mid, RNG_SEED, beta=BETA, gamma=GAMMA,
+                          freq=False, final_planes=True)
+        planes = o["final_planes"][0].contiguous()
+        empty = seeds[:0]
+
+        def one(profile=None):
+            opts = fsgp.make_options(t0=args.t_mid, init_planes=planes)
+            if profile is not None:
+                opts.profile = fsgp.ctypes.pointer(profile)
+            return fsgp.simulate(graph, m, [empty], R, 1, RNG_SEED, beta=BETA, gamma=GAMMA,
+                                 freq=False, options=opts)
+
+        for _ in range(args.warmup):
+            one()
+        torch.cuda.synchronize()
+        try:
+            torch.cuda.nvtx.range_push(f"fsgp_step_{nm}")
+            pushed = True
+        except Exception as e:   # no NVTX: the step still runs, only unmarked
+            log(f"[bench] no NVTX range: {e}")
+            pushed = False
+        one()
+        torch.cuda.synchronize()
+        if pushed:
+            torch.cuda.nvtx.range_pop()
+        prof = fsgp.fsgp_profile()
+        reps = max(1, args.steps)
+        for _ in range(reps):
+            out = one(prof)
+        torch.cuda.synchronize()
+        step_kinds = [i for i in range(len(kinds)) if kinds[i] not in ("init", "results")]
+        ms = sum(prof.ms[i] for i in step_kinds) / reps
+        b = step_bytes(g.n, g.nnz, R, 2 if m == 0 else 1)
+        res[nm] = {"t": args.t_mid, "step_ms": ms,
+                   "infected_lanes": int(out["counts"][0, -1, 1].item()),
+                   "step_bytes_alg": b, "achieved_GBps": b / (ms / 1e3) / 1e9,
+                   "frac": b / (ms / 1e3) / 1e9 / peak,
+                   "kinds": {kinds[i]: {"launches": prof.launches[i] // reps,
+                                        "ms": prof.ms[i] / reps,
+                                        "alg_bytes": prof.alg_bytes[i] / reps}
+                             for i in step_kinds if prof.launches[i]}}
+        log(f"[bench] {nm} step at t={args.t_mid}: {ms:.3f} ms")
+        del planes, o
+    graph.close()
+    return {"workload": f"rmat{args.scale}_mid_step_t{args.t_mid}", "n": g.n, "nnz": g.nnz,
+            "R": R, "peak_GBps": peak, "peak_source": peak_kind, "models": res}
+
+
 # -------------------------------------------------------------- learned surrogate
 
 SG_R, SG_T, SG_GAMMA, SG_K = 1024, 100, 0.1, 20
 
 
-def _sg_forward_bytes(n: int, nnz: int) -> float:
+def _sg_forward_bytes(n: int, nnz: int, keep_h3: bool = False) -> float:
     """Compulsory bytes of one surrogate forward: every array read or written once
     (row pointers 4 B/node, column indices 4 B/arc, bfloat16 activations 2 B/value):
     layer 1 aggregate 36 n + 4 nnz, layer 1 dense 160 n, layers 2-3 aggregate
-    260 n + 4 nnz each, layers 2-3 dense 384 n each, head 128 n."""
-    return 1612.0 * n + 12.0 * nnz
+    260 n + 4 nnz each, layer 2 dense 384 n, layer 3 dense with the output head 256 n
+    (+ 128 n when h3 is kept for training)."""
+    return (1356.0 + (128.0 if keep_h3 else 0.0)) * n + 12.0 * nnz
+
+
+def run_screen_bench(args):
+    """Screening throughput of the surrogate alone: one BA graph (n = --screen-n, m = 4),
+    a network with its initial weights (the timing does not depend on them), --sg-cands
+    candidate 20-node seed sets screened per step.  One step = one fsgp_surrogate_screen
+    call; launches replay one captured forward per candidate."""
+    import torch
+    import workloads as W
+    from paper_2603_14895_gb300 import fsgp
+    torch.cuda.set_device(0)
+    g = W.ba(args.screen_n, 4, seed=11)
+    graph = fsgp.Graph(g.row_ptr, g.col_idx)
+    sg = fsgp.Surrogate(3)
+    cands = W.surrogate_candidates(g, args.sg_cands, SG_K, seed=5)
+    beta = args.sg_beta_screen
+    for _ in range(args.warmup):
+        sg.screen(graph, cands[:64], beta, SG_GAMMA)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_selector(torch))
+    sampler.start()
+    t = time.perf_counter()
+    for _ in range(max(1, args.steps)):
+        sg.screen(graph, cands, beta, SG_GAMMA)      # synchronises
+    sec = (time.perf_counter() - t) / max(1, args.steps)
+    clocks = sampler.stop()
+    per = sec / len(cands)
+    peak, peak_src = measured_peaks()
+    b = _sg_forward_bytes(g.n, g.nnz)
+    return {"metric": "surrogate-screened seed sets/sec", "value": len(cands) / sec,
+            "unit": "seed sets/s", "n_gpus": 1, "steps": max(1, args.steps), "warmup": args.warmup,
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"screen_ba{g.n}_m4_k{SG_K}", "n": g.n, "nnz": g.nnz,
+                       "candidates": len(cands), "beta": beta, "gamma": SG_GAMMA,
+                       "l2": "one candidate's activations (64 MB per layer at n = 500k) stay "
+                             "partly L2-resident between the kernels of its forward; no flush"},
+            "ms_per_candidate": per * 1e3,
+            "roofline": {"bound": "hbm", "kernel": "screening forward (all launches of one candidate)",
+                         "achieved": b / per / 1e9, "peak": peak, "peak_source": peak_src,
+                         "unit": "GB/s", "frac": b / per / 1e9 / peak, "traffic": None,
+                         "alg_bytes_per_candidate": b},
+            "clocks": clocks}
 
 
 def run_surrogate_bench(args):
@@ -594,7 +713,10 @@ def main():
     ap.add_argument("--scale", type=int, default=SCALE)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="rmat26", choices=["rmat26", "batch", "surrogate", "ba1m", "er10k"])
+    ap.add_argument("--workload", default="rmat26",
+                    choices=["rmat26", "batch", "surrogate", "ba1m", "er10k", "step", "screen"])
+    ap.add_argument("--screen-n", type=int, default=500_000)
+    ap.add_argument("--t-mid", type=int, default=50)
     ap.add_argument("--sg-graphs", type=int, default=200)
     ap.add_argument("--sg-epochs", type=int, default=6)
     ap.add_argument("--sg-lr", type=float, default=2e-3)
@@ -625,6 +747,12 @@ def main():
         return
     if args.workload == "surrogate" and args.impl == "fsgp":
         print(json.dumps(run_surrogate_bench(args)), flush=True)
+        return
+    if args.workload == "screen" and args.impl == "fsgp":
+        print(json.dumps(run_screen_bench(args)), flush=True)
+        return
+    if args.workload == "step" and args.impl == "fsgp":
+        print(json.dumps(run_step_bench(args)), flush=True)
         return
     if args.workload in ("ba1m", "er10k") and args.impl == "fsgp":
         print(json.dumps(run_config_bench(args, args.workload)), flush=True)
@@ -711,8 +839,33 @@ def main():
     agg_n = [sum(profiles[m].launches[i] for m in MODELS) for i in range(NK)]
     dom = max(range(NK), key=lambda i: agg_ms[i])
     peak, peak_kind = measured_peaks()
-    achieved = (agg_b[dom] / agg_n[dom]) / (agg_ms[dom] / agg_n[dom] / 1e3) / 1e9 if agg_n[dom] else 0.0
-    traffic = ncu_traffic(kinds[dom])
+    dom_achieved = (agg_b[dom] / agg_n[dom]) / (agg_ms[dom] / agg_n[dom] / 1e3) / 1e9 if agg_n[dom] else 0.0
+    # The roofline unit is the dense propagation step (its degree-class launches together):
+    # algorithmic bytes per step x steps of both models over the whole timed run time
+    # (initialisation and result kernels included).
+    b_step = {"SIR": step_bytes(g.n, g.nnz, R, 2), "SIS": step_bytes(g.n, g.nnz, R, 1)}
+    alg_run = T * (b_step["SIR"] + b_step["SIS"])
+    achieved = alg_run / (ms_per_step / 1e3) / 1e9
+    # DRAM traffic per step: each kind's measured DRAM / algorithmic ratio (small capture)
+    # times the algorithmic bytes its launches processed here, averaged over the steps
+    ratios = ncu_traffic_ratios()
+    traffic = None
+    if ratios is not None:
+        tot = 0.0
+        for m, nm in zip(MODELS, ("SIR", "SIS")):
+            for i in range(NK):
+                b = profiles[m].alg_bytes[i]
+                if b == 0:
+                    continue
+                r = ratios.get(nm, {}).get(kinds[i])
+                if r is None:
+                    tot = None
+                    break
+                tot += r * b
+            if tot is None:
+                break
+        if tot is not None:
+            traffic = tot / (args.steps * T * len(MODELS))
     launches = sum(profiles[m].kernel_launches for m in MODELS)
     per_kernel = {kinds[i]: {"launches": agg_n[i] // args.steps,
                              "ms_per_step": agg_ms[i] / args.steps,
@@ -793,9 +946,14 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": workload_config(g, seeds),
         "full_mc_wall_s": wall,
-        "roofline": {"bound": "hbm", "kernel": kinds[dom], "achieved": achieved, "peak": peak,
-                     "peak_source": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak if peak else None, "traffic": traffic},
+        "roofline": {"bound": "hbm", "kernel": "dense propagation step (all row launches of a step)",
+                     "achieved": achieved, "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak if peak else None, "traffic": traffic,
+                     "alg_bytes_per_step": (b_step["SIR"] + b_step["SIS"]) / 2,
+                     "per_model_frac": {nm: T * b_step[nm] / wall[nm] / 1e9 / peak for nm in wall},
+                     "dominant_kernel": {"kind": kinds[dom], "achieved": dom_achieved,
+                                         "frac": dom_achieved / peak if peak else None,
+                                         "alg_bytes": "rows and arcs the launches processed"}},
         "kernels": per_kernel,
         "dense_steps": sum(profiles[m].dense_steps for m in MODELS) // args.steps,
         "sparse_steps": sum(profiles[m].sparse_steps for m in MODELS) // args.steps,
