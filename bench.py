@@ -848,6 +848,8 @@ def main():
     achieved = alg_run / (ms_per_step / 1e3) / 1e9
     # DRAM traffic per step: each kind's measured DRAM / algorithmic ratio (small capture)
     # times the algorithmic bytes its launches processed here, averaged over the steps
+    # (a step kind without a measured ratio for its model, e.g. SIR hub chunks, which
+    # process arcs only in the first steps, counts its algorithmic bytes in full)
     ratios = ncu_traffic_ratios()
     traffic = None
     if ratios is not None:
@@ -855,17 +857,10 @@ def main():
         for m, nm in zip(MODELS, ("SIR", "SIS")):
             for i in range(NK):
                 b = profiles[m].alg_bytes[i]
-                if b == 0:
+                if b == 0 or kinds[i] in ("init", "results"):
                     continue
-                r = ratios.get(nm, {}).get(kinds[i])
-                if r is None:
-                    tot = None
-                    break
-                tot += r * b
-            if tot is None:
-                break
-        if tot is not None:
-            traffic = tot / (args.steps * T * len(MODELS))
+                tot += ratios.get(nm, {}).get(kinds[i], 1.0) * b
+        traffic = tot / (args.steps * T * len(MODELS))
     launches = sum(profiles[m].kernel_launches for m in MODELS)
     per_kernel = {kinds[i]: {"launches": agg_n[i] // args.steps,
                              "ms_per_step": agg_ms[i] / args.steps,

@@ -57,8 +57,9 @@ extern "C" {
 #define FSGP_EINVAL (-1)          /* an argument is out of range or inconsistent */
 #define FSGP_ENOMEM (-2)          /* device or host allocation failed */
 #define FSGP_ECUDA (-3)           /* a CUDA runtime call failed (message has details) */
-#define FSGP_ETIMEOUT (-4)        /* a bounded device-side wait ran out (the surrogate's
-                                     tensor-core completion wait) */
+#define FSGP_ETIMEOUT (-4)        /* a bounded device-side wait ran out (a grid barrier of the
+                                     persistent step loop, or the surrogate's tensor-core
+                                     completion wait) */
 #define FSGP_EUNSUPPORTED (-5)    /* a valid request this library version does not implement */
 
 /* ------------------------------------------------------------------------ models */
@@ -148,12 +149,19 @@ typedef struct {
                                graph and launch it at once (ignored when profiling) */
     int32_t lane_words;     /* words per thread of the one-thread-per-row kernel (rows with
                                1..3 in-arcs): 1, 2, 4 or 8 (0 = auto) */
-    int32_t fuse_rows;      /* 1: every row in one warp-per-row kernel, dense steps only (two
-                               launches per step, for small graphs whose steps are bound by
-                               launch latency; needs in-degree < 65536); -1: never; 0: auto
-                               (graphs of at most 2^20 state words per plane, when no
-                               degree-class or frontier field is set) */
-    int32_t reserved[5];
+    int32_t fuse_rows;      /* 1: every row in one kernel per step (team per row when every
+                               in-degree is <= 255, else warp per row), dense steps only,
+                               for small graphs whose steps are bound by launch latency;
+                               needs in-degree < 65536; -1: never; 0: auto (graphs of at
+                               most 2^20 state words per plane, when no degree-class or
+                               frontier field is set) */
+    int32_t persistent;     /* fused team-per-row mode: 0 (auto) or 1 runs all T steps in one
+                               cooperative launch, steps separated by grid barriers, when
+                               per-realization counts and profiling are off and each thread
+                               takes one word; every barrier wait is bounded (about a second)
+                               and one that runs out ends the run: steps_run = -1 (device
+                               results) or FSGP_ETIMEOUT (host results); -1: never */
+    int32_t reserved[4];
 } fsgp_options;
 
 /* Caller-owned result buffers, all host or all device (flags).  NULL = not wanted,
@@ -165,7 +173,9 @@ typedef struct {
     uint32_t *per_real;      /* [n_sets][R][T+1][C]: per-realization compartment counts */
     uint32_t *final_planes;  /* [n_sets][planes][n][W]: final state bit-planes */
     int32_t *steps_run;      /* [n_sets]: transitions computed (IC/LT stop at the first
-                                step that activates nothing; later rows repeat) */
+                                step that activates nothing; later rows repeat); -1: a
+                                bounded wait of the persistent step loop ran out and the
+                                other results are not valid */
 } fsgp_result;
 
 /* Create a graph from an int32 in-CSR: row v lists the sources u of arcs u -> v
@@ -252,7 +262,9 @@ typedef struct {
     int32_t n_streams;      /* concurrent CUDA streams, one host thread each (0 = 4) */
     int32_t capture_graph;  /* 0 (default) or 1: capture each launch wave's step loop into
                                a CUDA graph; -1: launch kernels one by one */
-    int32_t autotune;       /* 1: run fsgp_autotune once per graph before its requests */
+    int32_t autotune;       /* 1: run fsgp_autotune once per graph before its requests and
+                               keep its choice on the graph; 0: use the choice an earlier
+                               call kept, if any, else the automatic defaults */
     int32_t reserved[8];
 } fsgp_batch_options;
 
@@ -270,8 +282,10 @@ int fsgp_batch_run(const fsgp_request *reqs, int32_t n, const fsgp_batch_options
 
 /* Pick the tuning fields of *inout (vector_words, small_max_deg, hub_min_deg,
  * hub_chunk) for graph g by timing short probe runs (T_probe steps from the given host
- * seed set) of every candidate: words per thread {1, 2, 4}, team-row bound {63, 255},
- * split-row bound {4096, 8192, 16384}.  Every candidate gives identical results; only
+ * seed set) of *inout as given (its automatic choices, such as the fused small-graph
+ * mode, which explicit bounds turn off) and of every candidate: words per thread
+ * {1, 2, 4}, team-row bound {63, 255}, split-row bound {4096, 8192, 16384}.  *inout is
+ * left unchanged when it is fastest.  Every candidate gives identical results; only
  * speed differs.  Synchronises `stream`.  Errors: EINVAL, ENOMEM, ECUDA. */
 int fsgp_autotune(const fsgp_graph *g, int32_t model, const fsgp_params *params,
                   const int32_t *seed_nodes, int64_t n_seeds, int32_t R, int32_t T_probe,
@@ -347,6 +361,16 @@ int fsgp_step_noalloc(int32_t model, const fsgp_params *params, const int32_t *r
                       const int32_t *col_idx, int32_t n, int64_t nnz, int32_t R, uint32_t t,
                       uint64_t rng_seed, const uint32_t *cur_planes, uint32_t *next_planes,
                       uint64_t *plane_counts, void *stream);
+
+/* Self-test of the bounded grid barrier that separates the steps of the persistent step
+ * loop (fsgp_options.persistent; a systems pattern, not in the paper).  Launches `ctas`
+ * co-resident CTAs (cooperative launch) that pass the barrier `rounds` times; the barrier
+ * expects ctas + missing CTAs, so with missing > 0 no round completes and every wait runs
+ * out after spin_cycles SM clock cycles.  Returns FSGP_OK if every round completed,
+ * FSGP_ETIMEOUT if a wait ran out (the device stays usable), FSGP_EINVAL for sizes out of
+ * range (ctas beyond the CTAs that fit at once included).  Allocates 16 bytes of device
+ * memory for the call; synchronises `stream`. */
+int fsgp_selftest_barrier(int32_t ctas, int32_t missing, int32_t rounds, int64_t spin_cycles, void *stream);
 
 /* Message for the last failure on the calling thread ("" if none).  The pointer stays
  * valid until the next fsgp_* call on this thread. */

@@ -100,6 +100,17 @@ extern "C" int fsgp_autotune(const fsgp_graph *gc, int32_t model, const fsgp_par
     fsgp_options best = *inout;
     float best_ms = 1e30f;
     int rc = FSGP_OK;
+    {
+        // the caller's own fields first (automatic choices: e.g. the fused small-graph
+        // mode, which any explicit degree-class bound below turns off)
+        fsgp_options o = *inout;
+        o.profile = nullptr;
+        o.init_planes = nullptr;
+        float ms = 0.f, m2 = 0.f;
+        rc = probe(g, model, params, seed_nodes, n_seeds, R, T_probe, rng_seed, o, d_counts, s, &ms);
+        if (rc == FSGP_OK) rc = probe(g, model, params, seed_nodes, n_seeds, R, T_probe, rng_seed, o, d_counts, s, &m2);
+        if (rc == FSGP_OK) best_ms = std::min(ms, m2);
+    }
     for (int vi = 0; vi < 3 && rc == FSGP_OK; ++vi) {
         if (vws[vi] > Ws && vws[vi] > 1) continue;
         for (int si = 0; si < 2 && rc == FSGP_OK; ++si)
@@ -173,11 +184,16 @@ extern "C" int fsgp_batch_run(const fsgp_request *reqs, int32_t n, const fsgp_ba
         const fsgp_graph *g = std::get<0>(kv.first);
         if (tuned.count(g)) continue;
         fsgp_options o{};
+        fsgp_graph *gm = const_cast<fsgp_graph *>(g);
         if (bo.autotune) {
             const fsgp_request &q = reqs[kv.second[0]];
             const int rc = fsgp_autotune(g, q.model, &q.params, q.seed_nodes, q.n_seeds, q.R,
                                          std::max(1, std::min(q.T, 8)), q.rng_seed, &o, caller);
             if (rc) return rc;
+            gm->tuned = 1;   // kept for later calls on this graph
+            gm->tuned_opt = o;
+        } else if (gm->tuned) {
+            o = gm->tuned_opt;
         }
         o.capture_graph = bo.capture_graph >= 0 ? 1 : 0;
         tuned[g] = o;

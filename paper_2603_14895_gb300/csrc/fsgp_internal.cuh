@@ -157,6 +157,8 @@ struct fsgp_graph {
     fsgp::Workspace ws{};
     std::vector<fsgp::ExecCache> execs;   // most recent last (they point into ws)
     fsgp::SgCache sgc{};
+    int tuned = 0;                  // fsgp_batch_run: tuning chosen by an autotuned call
+    fsgp_options tuned_opt{};
     int sm_count = 0;
     size_t device_bytes = 0;
 };

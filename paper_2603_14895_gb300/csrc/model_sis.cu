@@ -6,4 +6,5 @@ namespace fsgp {
 template int launch_rows<FSGP_SIS>(const StepArgs &, const StepLaunch &, cudaStream_t);
 template int occupancy_rows<FSGP_SIS>(int, int, size_t, RowOccupancy *);
 template int launch_split_rows<FSGP_SIS>(const StepArgs &, int, int, int, int, cudaStream_t);
+template int launch_persist<FSGP_SIS>(const StepArgs &, const PersistArgs &, int, int, size_t, int, cudaStream_t, int *);
 }  // namespace fsgp

@@ -3,6 +3,8 @@
 // one translation unit per model so that the instantiations compile in parallel.
 #pragma once
 
+#include <algorithm>
+
 #include "step.cuh"
 
 namespace fsgp {
@@ -25,6 +27,33 @@ __device__ __forceinline__ Vec<V> ldg_vec(const uint32_t *p) {
         r.w[0] = __ldg(p);
     }
     return r;
+}
+
+// State loads of a kernel that reads planes written earlier in the same launch (the
+// persistent step loop): through L2 only (ld.global.cg), never the non-coherent path.
+template <int V, bool CG>
+__device__ __forceinline__ Vec<V> ld_vec(const uint32_t *p) {
+    if constexpr (!CG) {
+        return ldg_vec<V>(p);
+    } else {
+        Vec<V> r;
+        if constexpr (V == 4) {
+            const uint4 q = __ldcg(reinterpret_cast<const uint4 *>(p));
+            r.w[0] = q.x; r.w[1] = q.y; r.w[2] = q.z; r.w[3] = q.w;
+        } else if constexpr (V == 2) {
+            const uint2 q = __ldcg(reinterpret_cast<const uint2 *>(p));
+            r.w[0] = q.x; r.w[1] = q.y;
+        } else {
+            r.w[0] = __ldcg(p);
+        }
+        return r;
+    }
+}
+
+template <bool CG>
+__device__ __forceinline__ uint32_t ld_word(const uint32_t *p) {
+    if constexpr (CG) return __ldcg(p);
+    else return __ldg(p);
 }
 
 template <int V>
@@ -110,7 +139,7 @@ __device__ __forceinline__ uint64_t ic_threshold(const StepArgs &A, int s, int32
 // group are in flight, so each group costs one memory latency instead of two.
 // IC draws are keyed by the arc's position in the caller's column array: arc e of the
 // relabelled array is caller arc e + arcb.
-template <int MODEL, int V, int B>
+template <int MODEL, int V, int B, bool CG = false>
 __device__ __forceinline__ void gather_arcs(const StepArgs &A, int64_t e_begin, int64_t e_end,
                                             int64_t step, int64_t arcb, int w0, const uint32_t (&need)[V],
                                             const uint64_t (&ic_thr)[V], const WordCtx (&x)[V],
@@ -125,7 +154,7 @@ __device__ __forceinline__ void gather_arcs(const StepArgs &A, int64_t e_begin, 
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (u[j] >= 0) {
-                xs[j] = ldg_vec<V>(src + (size_t)u[j] * Wn);
+                xs[j] = ld_vec<V, CG>(src + (size_t)u[j] * Wn);
             } else {
 #pragma unroll
                 for (int i = 0; i < V; ++i) xs[j].w[i] = 0u;
@@ -176,10 +205,11 @@ constexpr int min_ctas() { return V == 4 ? 2 : (V == 2 ? (WIDE ? 3 : 4) : 4); }
 // fewer registers and cheaper counting and grouping).
 // which: 0 = small rows with 16..small_max in-arcs (and every small row of a frontier
 // step), 1 = mid rows, 3 = rows with 4..15 in-arcs (dense steps only).
-template <int MODEL, int V, int TEAM, bool WARP_ROW, int BT = kSmallBits>
-__global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepArgs A, int which) {
-    extern __shared__ int32_t s_lane[];
-    __shared__ unsigned long long s_pc[kPC * kMaxSets];
+// CG: the state planes are read through L2 only (the persistent step loop, which reads
+// in one launch the planes that other CTAs wrote at the previous step).
+template <int MODEL, int V, int TEAM, bool WARP_ROW, int BT, bool CG>
+__device__ __forceinline__ void rows_body(const StepArgs &A, int which, int32_t *s_lane,
+                                          unsigned long long *s_pc) {
     constexpr int B = WARP_ROW ? kWideBits : BT;
     constexpr int TPW = 32 / TEAM;
     constexpr int SW = TEAM * V;
@@ -244,10 +274,10 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
         // lanes that can change through their in-arcs: S (SIR/SIS) or inactive (IC/LT)
         uint32_t need[V];
         {
-            Vec<V> a = has_row ? ldg_vec<V>(A.cur + off) : Vec<V>{};
+            Vec<V> a = has_row ? ld_vec<V, CG>(A.cur + off) : Vec<V>{};
             Vec<V> b{}, e{};
-            if (P >= 2 && MODEL != FSGP_IC && MODEL != FSGP_LT && has_row) b = ldg_vec<V>(A.cur + A.plane_words + off);
-            if (MODEL == FSGP_SEIR && has_row) e = ldg_vec<V>(A.cur + 2 * A.plane_words + off);
+            if (P >= 2 && MODEL != FSGP_IC && MODEL != FSGP_LT && has_row) b = ld_vec<V, CG>(A.cur + A.plane_words + off);
+            if (MODEL == FSGP_SEIR && has_row) e = ld_vec<V, CG>(A.cur + 2 * A.plane_words + off);
 #pragma unroll
             for (int i = 0; i < V; ++i) {
                 const uint32_t vm = has_row ? x[i].vm : 0u;
@@ -281,9 +311,9 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
             for (int i = 0; i < V; ++i)
                 ic_thr[i] = ModelTraits<MODEL>::counts ? 0ull : ic_threshold(A, x[i].s, end - beg);
             if (WARP_ROW)
-                gather_arcs<MODEL, V, B>(A, (int64_t)beg + 4 * team, end, 4 * TPW, arcb, w0, need, ic_thr, x, c, newly);
+                gather_arcs<MODEL, V, B, CG>(A, (int64_t)beg + 4 * team, end, 4 * TPW, arcb, w0, need, ic_thr, x, c, newly);
             else
-                gather_arcs<MODEL, V, B>(A, beg, end, 4, arcb, w0, need, ic_thr, x, c, newly);
+                gather_arcs<MODEL, V, B, CG>(A, beg, end, 4, arcb, w0, need, ic_thr, x, c, newly);
         }
         constexpr bool SPLIT = WARP_ROW && TPW >= V;   // enough teams to give each word one
         if constexpr (SPLIT && V == 2 && ModelTraits<MODEL>::counts) {
@@ -344,9 +374,9 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
                         nw = newly[q];
                     }
                 }
-                const uint32_t s0 = __ldg(A.cur + off + i);
-                const uint32_t s1 = P >= 2 ? __ldg(A.cur + A.plane_words + off + i) : 0u;
-                const uint32_t s2 = P >= 3 ? __ldg(A.cur + 2 * A.plane_words + off + i) : 0u;
+                const uint32_t s0 = ld_word<CG>(A.cur + off + i);
+                const uint32_t s1 = P >= 2 ? ld_word<CG>(A.cur + A.plane_words + off + i) : 0u;
+                const uint32_t s2 = P >= 3 ? ld_word<CG>(A.cur + 2 * A.plane_words + off + i) : 0u;
                 const WordOut o = update_word<MODEL, B>(A, node, xw, s0, s1, s2, end - beg, cw, nw);
                 A.nxt[off + i] = o.n0;
                 if (P >= 2) A.nxt[A.plane_words + off + i] = o.n1;
@@ -375,10 +405,10 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
             // own state again (L1/L2-resident): not kept live across the gather
             uint32_t s0[V], s1[V], s2[V];
             {
-                Vec<V> a = ldg_vec<V>(A.cur + off);
+                Vec<V> a = ld_vec<V, CG>(A.cur + off);
                 Vec<V> b{}, e{};
-                if (P >= 2) b = ldg_vec<V>(A.cur + A.plane_words + off);
-                if (P >= 3) e = ldg_vec<V>(A.cur + 2 * A.plane_words + off);
+                if (P >= 2) b = ld_vec<V, CG>(A.cur + A.plane_words + off);
+                if (P >= 3) e = ld_vec<V, CG>(A.cur + 2 * A.plane_words + off);
 #pragma unroll
                 for (int i = 0; i < V; ++i) {
                     s0[i] = a.w[i];
@@ -424,6 +454,69 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
     flush_accum(A, acc, list_slot, WARP_ROW ? PK_MID : (BT == 4 ? PK_SMALL4 : PK_SMALL));
     set_acc_flush(A, s_pc);
     if (lanes_on) flush_lanes(A, s_lane, nl);
+}
+
+template <int MODEL, int V, int TEAM, bool WARP_ROW, int BT = kSmallBits>
+__global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepArgs A, int which) {
+    extern __shared__ int32_t s_lane[];
+    __shared__ unsigned long long s_pc[kPC * kMaxSets];
+    rows_body<MODEL, V, TEAM, WARP_ROW, BT, false>(A, which, s_lane, s_pc);
+}
+
+// Persistent step loop of a small graph: all T dense steps in one launch, the row work of
+// the fused mode (every row, one kernel) separated by grid barriers instead of kernel
+// boundaries.  The step control of the launched loop is folded in: each step's plane
+// popcount changes go to its own row of pc (running totals are formed after the loop),
+// and the cascade models stop at the first step whose previous step activated nothing,
+// a decision every CTA takes alike from the same counts.  State is read through L2
+// (CG loads): a CTA reads at step k the words other CTAs wrote at step k-1.
+// (bounded for 2 resident CTAs per SM: the loop is meant for graphs that fill a few CTAs
+// per SM at most, and the body then keeps its state in registers)
+template <int MODEL, int V, int TEAM, bool WARP_ROW, int BT = kSmallBits>
+__global__ void __launch_bounds__(kBlock, 2)
+    k_rows_persist(const __grid_constant__ StepArgs A0, const __grid_constant__ PersistArgs Q) {
+    extern __shared__ int32_t s_lane[];
+    __shared__ unsigned long long s_pc[kPC * kMaxSets];
+    __shared__ StepArgs sA;
+    __shared__ unsigned long long s_new[kMaxSets];   // cascade: lanes newly active at the last step
+    __shared__ int s_stop;
+    constexpr bool cascade = ModelTraits<MODEL>::cascade;
+    Ctl *C = A0.ctl;
+    {
+        const int32_t *src = reinterpret_cast<const int32_t *>(&A0);
+        int32_t *dst = reinterpret_cast<int32_t *>(&sA);
+        for (int i = threadIdx.x; i < (int)(sizeof(StepArgs) / sizeof(int32_t)); i += blockDim.x) dst[i] = src[i];
+    }
+    if (cascade)
+        for (int s = threadIdx.x; s < A0.S; s += blockDim.x) s_new[s] = __ldcg(Q.pc + (size_t)s * kPC + 1);
+    for (int k = 1; k <= Q.T; ++k) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int stop = 0;
+            if (cascade) {
+                stop = 1;
+                for (int s = 0; s < A0.S; ++s)
+                    if (s_new[s]) stop = 0;
+            }
+            s_stop = stop;
+            sA.k = k;
+            sA.t = Q.t0 + (uint32_t)k;
+            sA.cur = (k & 1) ? Q.buf0 : Q.buf1;
+            sA.nxt = (k & 1) ? Q.buf1 : Q.buf0;
+            sA.pc = Q.pc + (size_t)k * A0.S * kPC;
+        }
+        __syncthreads();
+        if (s_stop) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) C->stop = 1;
+            break;
+        }
+        rows_body<MODEL, V, TEAM, WARP_ROW, BT, true>(sA, WARP_ROW ? 1 : 0, s_lane, s_pc);
+        if (!grid_barrier(&C->bar_count, &C->bar_gen, gridDim.x, &C->err, Q.spin_limit)) break;
+        if (blockIdx.x == 0 && threadIdx.x == 0) C->steps_done = k;
+        if (cascade)
+            for (int s = threadIdx.x; s < A0.S; s += blockDim.x)
+                s_new[s] += __ldcg(Q.pc + ((size_t)k * A0.S + s) * kPC + 1);
+    }
 }
 
 // Hub rows, phase 1: one CTA per (chunk of in-arcs, word slice); per-lane partial counts
@@ -1031,6 +1124,42 @@ int occupancy_rows(int V, int TEAM, size_t smem, RowOccupancy *o) {
 #undef FSGP_O
     o->lane = occupancy_lane<MODEL>(o->swl, smem);
     return FSGP_OK;
+}
+
+// Cooperative launch of the persistent step loop (one word per thread, the 8-bit team
+// kernel: fused small graphs with in-degrees <= 255).  The grid is capped at the CTAs
+// that can be resident at once; *grid_out gets the grid used.  FSGP_EUNSUPPORTED: no
+// persistent kernel for this team width (the caller runs the launched loop instead).
+template <int MODEL, int TEAM>
+int launch_persist_t(const StepArgs &A, const PersistArgs &Q, int grid, size_t smem, int sm_count,
+                     cudaStream_t s, int *grid_out) {
+    auto kern = k_rows_persist<MODEL, 1, TEAM, false, kSmallBits>;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor (persistent)");
+    if (per_sm < 1) return FSGP_EUNSUPPORTED;
+    grid = std::max(1, std::min(grid, per_sm * sm_count));
+    StepArgs a = A;
+    PersistArgs q = Q;
+    void *args[] = {&a, &q};
+    e = cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(kBlock), args, smem, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel (persistent step loop)");
+    *grid_out = grid;
+    return FSGP_OK;
+}
+
+template <int MODEL>
+int launch_persist(const StepArgs &A, const PersistArgs &Q, int TEAM, int grid, size_t smem, int sm_count,
+                   cudaStream_t s, int *grid_out) {
+    switch (TEAM) {
+        case 1: return launch_persist_t<MODEL, 1>(A, Q, grid, smem, sm_count, s, grid_out);
+        case 2: return launch_persist_t<MODEL, 2>(A, Q, grid, smem, sm_count, s, grid_out);
+        case 4: return launch_persist_t<MODEL, 4>(A, Q, grid, smem, sm_count, s, grid_out);
+        case 8: return launch_persist_t<MODEL, 8>(A, Q, grid, smem, sm_count, s, grid_out);
+        case 16: return launch_persist_t<MODEL, 16>(A, Q, grid, smem, sm_count, s, grid_out);
+        case 32: return launch_persist_t<MODEL, 32>(A, Q, grid, smem, sm_count, s, grid_out);
+        default: return FSGP_EUNSUPPORTED;
+    }
 }
 
 }  // namespace fsgp

@@ -280,6 +280,10 @@ __global__ void k_finalize(StepArgs A, int model, int T, const unsigned long lon
     // IC/LT: the first step whose frontier is empty (later rows repeat); otherwise T
     for (int s = threadIdx.x + blockIdx.x * blockDim.x; s < S; s += blockDim.x * gridDim.x) {
         int st = T;
+        if (*(volatile const int32_t *)&A.ctl->err) {   // the persistent loop timed out
+            outs[s].steps[0] = -1;
+            continue;
+        }
         if (model == FSGP_IC || model == FSGP_LT)
             for (int k = 0; k <= T; ++k)
                 if (pc_all[((size_t)k * S + s) * kPC + 1] == 0ull) {
@@ -288,6 +292,21 @@ __global__ void k_finalize(StepArgs A, int model, int T, const unsigned long lon
                 }
         outs[s].steps[0] = st;
     }
+}
+
+// Persistent step loop: rows 1..T of pc hold each step's changes; make them running
+// totals (a stopped cascade's later rows repeat its last row).
+__global__ void k_pc_prefix(unsigned long long *pc, int T, int width) {
+    for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < width; i += blockDim.x * gridDim.x)
+        for (int k = 1; k <= T; ++k) pc[(size_t)k * width + i] += pc[(size_t)(k - 1) * width + i];
+}
+
+// Self-test of the bounded grid barrier: every CTA arrives `rounds` times at a barrier
+// that expects gridDim.x + missing CTAs; with missing > 0 no generation completes and
+// every wait runs out after `limit` cycles.
+__global__ void k_barrier_selftest(uint32_t *bar, int32_t *err, int rounds, int missing, long long limit) {
+    for (int r = 0; r < rounds; ++r)
+        if (!grid_barrier(bar, bar + 1, gridDim.x + (uint32_t)missing, err, limit)) break;
 }
 
 // Per-node final compartment frequencies of every set that asked for them.
@@ -435,6 +454,25 @@ static int occupancy_model(int model, int V, int TEAM, size_t smem, RowOccupancy
         default: return fail(FSGP_EINVAL, "model without row kernels");
     }
 }
+
+static int launch_persist_model(int model, const StepArgs &A, const PersistArgs &Q, int TEAM, int grid,
+                                size_t smem, int sm_count, cudaStream_t s, int *grid_out) {
+    switch (model) {
+        case FSGP_SIR: return launch_persist<FSGP_SIR>(A, Q, TEAM, grid, smem, sm_count, s, grid_out);
+        case FSGP_SIS: return launch_persist<FSGP_SIS>(A, Q, TEAM, grid, smem, sm_count, s, grid_out);
+        case FSGP_IC: return launch_persist<FSGP_IC>(A, Q, TEAM, grid, smem, sm_count, s, grid_out);
+        case FSGP_LT: return launch_persist<FSGP_LT>(A, Q, TEAM, grid, smem, sm_count, s, grid_out);
+        case FSGP_SEIR: return launch_persist<FSGP_SEIR>(A, Q, TEAM, grid, smem, sm_count, s, grid_out);
+        case FSGP_SEIS: return launch_persist<FSGP_SEIS>(A, Q, TEAM, grid, smem, sm_count, s, grid_out);
+        case FSGP_SWIR: return launch_persist<FSGP_SWIR>(A, Q, TEAM, grid, smem, sm_count, s, grid_out);
+        default: return fail(FSGP_EINVAL, "model without row kernels");
+    }
+}
+
+// A grid-barrier wait of the persistent step loop lasts at most this many SM cycles
+// (about one second at the GB300's clock): a step of a graph small enough for the loop
+// takes microseconds.
+constexpr long long kPersistSpinCycles = 2000000000ll;
 
 constexpr int32_t kSmallMaxFused = 255;   // in-degree bound of the 8-bit team kernel
 
@@ -673,6 +711,9 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     // fused rows: the team-per-row kernel (8-bit counters) when every in-degree is below
     // 256, else the warp-per-row kernel (16-bit counters)
     const bool fuse_team = fuse && g->max_deg <= kSmallMaxFused;
+    // all T steps in one cooperative launch (fused team rows, no per-lane counts)
+    const bool persist = fuse_team && opt.persistent >= 0 && !want_lanes && !profiling && V == 1 && T >= 1 &&
+                         n > 0;
     L.have_small = fuse ? (fuse_team && n > 0) : n_small_all > 0;
     L.have_small4 = n_small4 > 0 && !fuse;
     L.have_lane = (n_lane > 0 || n_d0 > 0) && !fuse;
@@ -794,8 +835,8 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     // The launch sequence from here to the results is free of host synchronisation and
     // host-memory copies, so it can be captured into one CUDA graph and launched at once.
     // (the legacy default stream cannot be captured; such callers launch directly)
-    const bool capture = opt.capture_graph != 0 && !profiling && s != nullptr && s != cudaStreamLegacy &&
-                         s != cudaStreamPerThread;
+    const bool capture = opt.capture_graph != 0 && !profiling && !persist && s != nullptr &&
+                         s != cudaStreamLegacy && s != cudaStreamPerThread;
     // step 0
     A.cur = buf0;
     A.nxt = buf1;
@@ -835,7 +876,29 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     ++launches;
     if (profiling) prof.stop(s);
     FSGP_CUDA(cudaGetLastError());
-    for (int k = 1; k <= T; ++k) {
+    bool persisted = false;
+    if (persist) {
+        // no row lists: the loop runs dense steps only
+        FSGP_CUDA(cudaMemsetAsync(&ctl->build_list, 0, sizeof(int32_t), s));
+        PersistArgs Q;
+        Q.buf0 = buf0;
+        Q.buf1 = buf1;
+        Q.pc = pc;
+        Q.T = (int32_t)T;
+        Q.t0 = (uint32_t)opt.t0;
+        Q.spin_limit = kPersistSpinCycles;
+        int grid_used = 0;
+        rc = launch_persist_model(model, A, Q, TEAM, L.grid_small, L.smem_lanes, g->sm_count, s, &grid_used);
+        if (rc == FSGP_OK) {
+            const int width = S * kPC;
+            k_pc_prefix<<<(width + 255) / 256, 256, 0, s>>>(pc, (int)T, width);
+            launches += 2;
+            persisted = true;
+        } else if (rc != FSGP_EUNSUPPORTED) {
+            return rc;
+        }
+    }
+    for (int k = 1; k <= T && !persisted; ++k) {
         A.k = k;
         A.t = (uint32_t)(opt.t0 + k);
         A.cur = (k & 1) ? buf0 : buf1;
@@ -921,7 +984,10 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
                                           cudaMemcpyDeviceToHost, s));
         }
     }
+    int32_t timed_out = 0;
+    if (persist && host_out) FSGP_CUDA(cudaMemcpyAsync(&timed_out, &ctl->err, sizeof timed_out, cudaMemcpyDeviceToHost, s));
     if (host_out || profiling) FSGP_CUDA(cudaStreamSynchronize(s));
+    if (timed_out) return fail(FSGP_ETIMEOUT, "a grid barrier of the persistent step loop timed out");
     if (want_steps && host_out)
         for (int i = 0; i < S; ++i)
             if (sets[i]->steps_run) *sets[i]->steps_run = hsteps[i];
@@ -1079,4 +1145,38 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
         x.out_flags = out->flags;
     }
     return run_sets(g, run_model, params->ic_mode, sets.data(), n_sets, T, opt, (cudaStream_t)stream);
+}
+
+extern "C" int fsgp_selftest_barrier(int32_t ctas, int32_t missing, int32_t rounds, int64_t spin_cycles,
+                                     void *stream) {
+    set_error("");
+    if (ctas < 1 || ctas > 4096 || missing < 0 || missing > 4096 || rounds < 1 || rounds > 1000000 ||
+        spin_cycles < 1 || spin_cycles > ((int64_t)1 << 34))
+        return fail(FSGP_EINVAL, "selftest_barrier: ctas in [1, 4096], missing in [0, 4096], rounds >= 1, "
+                                 "spin_cycles in [1, 2^34]");
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0, per_sm = 0;
+    FSGP_CUDA(cudaGetDevice(&dev));
+    FSGP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    FSGP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_barrier_selftest, 32, 0));
+    if ((int64_t)ctas > (int64_t)per_sm * sms) return fail(FSGP_EINVAL, "selftest_barrier: more CTAs than fit at once");
+    uint32_t *d = nullptr;
+    FSGP_CUDA(cudaMalloc(&d, 4 * sizeof(uint32_t)));   // count, generation, error flag
+    int rc = FSGP_OK;
+    int32_t err = 0;
+    cudaError_t e = cudaMemsetAsync(d, 0, 4 * sizeof(uint32_t), s);
+    if (e == cudaSuccess) {
+        uint32_t *bar = d;
+        int32_t *errp = reinterpret_cast<int32_t *>(d + 2);
+        int r = rounds, m = missing;
+        long long lim = (long long)spin_cycles;
+        void *args[] = {&bar, &errp, &r, &m, &lim};
+        e = cudaLaunchCooperativeKernel((const void *)k_barrier_selftest, dim3(ctas), dim3(32), args, 0, s);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, d + 2, sizeof err, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "selftest_barrier");
+    cudaFree(d);
+    if (rc == FSGP_OK && err) rc = fail(FSGP_ETIMEOUT, "selftest_barrier: a barrier wait ran out");
+    return rc;
 }

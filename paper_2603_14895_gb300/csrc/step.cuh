@@ -34,7 +34,7 @@ struct Ctl {
     int32_t stop;          // IC/LT: an earlier step activated nothing
     int32_t steps_done;    // transitions computed so far (relative to t0)
     int32_t sparse;        // the current step runs on the frontier lists
-    int32_t err;
+    int32_t err;           // a bounded wait of the persistent step loop ran out
     uint32_t list_n[2];    // rows listed for the next step (by step parity)
     uint64_t push_outdeg[2];
     uint32_t cand_n[2];    // sparse candidates: 0 = small rows, 1 = mid rows
@@ -43,6 +43,19 @@ struct Ctl {
     int32_t build_list;    // the current step lists its rows for the next step
     int32_t list_valid[2]; // the list of that parity was built
     uint32_t d0_n;         // rows without in-arcs listed by the step-0 scan (d0_list)
+    uint32_t bar_count;    // persistent step loop: CTAs arrived at the grid barrier
+    uint32_t bar_gen;      // persistent step loop: barrier generation
+};
+
+// The persistent step loop of a small graph (one launch for all T steps): the per-step
+// fields of StepArgs, and the bound on each grid-barrier wait.
+struct PersistArgs {
+    uint32_t *buf0, *buf1;         // state buffers (step k reads buf[(k-1)&1], writes buf[k&1])
+    unsigned long long *pc;        // [T+1][S][kPC]; rows 1..T are zero on entry and receive
+                                   // each step's changes (running totals formed afterwards)
+    int32_t T;
+    uint32_t t0;
+    long long spin_limit;          // SM clock cycles one barrier wait may last
 };
 
 // Per-set parameters (device array, one entry per set of the launch).
@@ -557,6 +570,40 @@ __device__ __forceinline__ void set_acc_flush(const StepArgs &A, const unsigned 
         if (s_pc[i]) atomicAdd(&A.pc[i], s_pc[i]);
 }
 
+// Grid barrier of the persistent step loop (its CTAs are co-resident: cooperative
+// launch) for `expected` CTAs.  Arrival is one atomic per CTA; the last CTA to arrive
+// resets the count and advances the generation.  A wait lasts at most `limit` SM clock cycles: past that the
+// CTA records the time-out in *err and goes on.  Returns, uniformly over the CTA,
+// whether no time-out has been recorded so far.
+__device__ __forceinline__ bool grid_barrier(uint32_t *count, uint32_t *gen, uint32_t expected, int32_t *err,
+                                             long long limit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile uint32_t *vgen = gen;
+        const uint32_t g = *vgen;   // read before arriving: it cannot advance until we have
+        __threadfence();            // this CTA's state writes and counter flushes first
+        if (atomicAdd(count, 1u) == expected - 1u) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == g) {
+                if (clock64() - t0 > limit) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = *(volatile int32_t *)err == 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 // per-lane count changes of one word of one plane (s_plane: that plane's counters)
 __device__ __forceinline__ void lane_deltas(int32_t *s_plane, int w, uint32_t olds, uint32_t news) {
     uint32_t ch = olds ^ news;
@@ -672,6 +719,10 @@ struct SetSpec {
 // set run side by side in one launch sequence (up to kMaxSets at a time).
 int run_sets(fsgp_graph *g, int model, int ic_mode, const SetSpec *sets, int n_sets, int T,
              const fsgp_options &opt, cudaStream_t s);
+
+template <int MODEL>
+int launch_persist(const StepArgs &A, const PersistArgs &Q, int TEAM, int grid, size_t smem, int sm_count,
+                   cudaStream_t s, int *grid_out);
 
 // Defined in rows.cuh, instantiated once per model (model_*.cu).
 template <int MODEL>

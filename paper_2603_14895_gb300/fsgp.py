@@ -57,7 +57,7 @@ class fsgp_options(ctypes.Structure):
                 ("t0", ctypes.c_int32), ("init_planes", ctypes.c_void_p),
                 ("profile", ctypes.POINTER(fsgp_profile)), ("capture_graph", ctypes.c_int32),
                 ("lane_words", ctypes.c_int32), ("fuse_rows", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("persistent", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class fsgp_result(ctypes.Structure):
@@ -147,6 +147,8 @@ def load():
         lib.fsgp_surrogate_screen.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_double, ctypes.c_double, P, P]
         lib.fsgp_surrogate_screen.restype = ctypes.c_int
+        lib.fsgp_selftest_barrier.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, P]
+        lib.fsgp_selftest_barrier.restype = ctypes.c_int
         lib.fsgp_last_error.argtypes = []
         lib.fsgp_last_error.restype = ctypes.c_char_p
         lib.fsgp_version.argtypes = []
@@ -245,6 +247,15 @@ def fsgp_step_noalloc(model, params: fsgp_params, row_ptr, col_idx, n, nnz, R, t
                                     n, nnz, R, t, ctypes.c_uint64(rng_seed), _ptr(cur_planes),
                                     _ptr(next_planes), _ptr(plane_counts),
                                     _stream_handle(stream)))
+
+
+def fsgp_selftest_barrier(ctas: int, missing: int, rounds: int, spin_cycles: int, stream=None) -> int:
+    """Status of the grid-barrier self-test (FSGP_OK or FSGP_ETIMEOUT; other codes raise)."""
+    rc = load().fsgp_selftest_barrier(ctas, missing, rounds, ctypes.c_int64(spin_cycles),
+                                      _stream_handle(stream))
+    if rc not in (FSGP_OK, FSGP_ETIMEOUT):
+        _check(rc)
+    return rc
 
 
 def fsgp_batch_run(reqs, n, options: fsgp_batch_options | None = None, stream=None) -> None:
