@@ -327,10 +327,16 @@ def run_config_bench(args, which: str):
         for _ in range(args.warmup):
             step()
     torch.cuda.synchronize()
+    # time at least about a second, so that the clock sampler sees the run
+    t_one = time.perf_counter()
+    with torch.cuda.stream(stream):
+        step()
+    torch.cuda.synchronize()
+    t_one = time.perf_counter() - t_one
+    reps = max(1, args.steps, int(1.0 / max(t_one, 1e-4)) + 1)
     sampler = ClockSampler(gpu_selector(torch))
     sampler.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = max(1, args.steps)
     with torch.cuda.stream(stream):
         ev0.record(stream)
         for _ in range(reps):
