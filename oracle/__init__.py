@@ -75,6 +75,13 @@ def _load():
                 ctypes.c_uint64, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                 ctypes.c_int, P, P, P, P, P]
             lib.orc_simulate_ext.restype = ctypes.c_int
+            lib.orc_simulate_w.argtypes = [
+                ctypes.c_int, ctypes.c_int32, P, P, ctypes.c_double, ctypes.c_double,
+                ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                P, P, ctypes.c_int64, ctypes.c_int32,
+                ctypes.c_uint64, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                ctypes.c_int, P, P, P, P, P]
+            lib.orc_simulate_w.restype = ctypes.c_int
             lib.orc_compartments.argtypes = [ctypes.c_int]
             lib.orc_compartments.restype = ctypes.c_int
             lib.orc_node_step.argtypes = [
@@ -132,10 +139,12 @@ class OracleResult:
 def simulate(model: int, row_ptr, col_idx, seeds, *, beta=0.0, gamma=0.0,
              ic_mode=IC_WEIGHTED_CASCADE, ic_p=0.0, alpha=0.0, mu=0.0, nu=0.0, R=1, T=0,
              rng_seed=0, r_lo=0, n_real=None, init_state=None, t0=0, nthreads=None,
-             outputs=("counts", "per_real", "freq", "final_state")) -> OracleResult:
+             outputs=("counts", "per_real", "freq", "final_state"), arc_weights=None) -> OracleResult:
     """Run realizations r_lo .. r_lo+n_real-1 of one seed set on the in-CSR graph.
     `outputs` limits which result arrays are produced (counts always are).  alpha is the
-    SEIR/SEIS latent rate (E -> I); SWIR takes kappa = beta, mu and nu."""
+    SEIR/SEIS latent rate (E -> I); SWIR takes kappa = beta, mu and nu.  arc_weights
+    (float32 per arc of col_idx, SIR/SIS/SI only): arc e infects with probability
+    beta * w_e per step (weighted graphs)."""
     lib = _load()
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
     col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
@@ -154,9 +163,13 @@ def simulate(model: int, row_ptr, col_idx, seeds, *, beta=0.0, gamma=0.0,
     if init_state is not None:
         init_state = np.ascontiguousarray(init_state, dtype=np.uint8)
         assert init_state.shape == (n_real, n)
-    rc = lib.orc_simulate_ext(int(model), n, _ptr(row_ptr), _ptr(col_idx), float(beta),
+    w = None
+    if arc_weights is not None:
+        w = np.ascontiguousarray(arc_weights, dtype=np.float32)
+        assert w.shape == (col_idx.shape[0],)
+    rc = lib.orc_simulate_w(int(model), n, _ptr(row_ptr), _ptr(col_idx), float(beta),
                               float(gamma), int(ic_mode), float(ic_p), float(alpha), float(mu),
-                              float(nu), _ptr(seeds), int(seeds.shape[0]), int(T), int(rng_seed),
+                              float(nu), _ptr(w), _ptr(seeds), int(seeds.shape[0]), int(T), int(rng_seed),
                               _ptr(init_state), int(t0), int(r_lo), int(n_real), int(nthreads),
                               _ptr(counts), _ptr(per_real), _ptr(freq), _ptr(final_state),
                               _ptr(quiet))

@@ -39,6 +39,15 @@
  *        S -> W iff k >= 1 and u(tag 6) >= surv_mu[k]; W -> I iff k >= 1 and u >=
  *        surv_nu[k]; I -> R at the next step.
  *    Every node changes state at most once per step, from its step-(t-1) state.
+ *  - Weighted graphs (Table 1 lists edge weights for the epidemic models; SIR, SIS and
+ *    SI here): arc e = (u -> v) carries weight w_e >= 0 and infects with probability
+ *    p_e = beta * w_e per step while u is infectious and v susceptible, independently
+ *    over arcs, so that v escapes with probability prod_e (1 - p_e) (the unweighted
+ *    1-(1-beta)^k when every w_e = 1).  Each infectious in-arc draws its own uniform
+ *    (tag 7, keyed by the arc's position e in col_idx, the step and the realization)
+ *    and transmits iff u < thr_e; thr_e is formed in single precision:
+ *    p = (float)beta * w_e, thr_e = 0 if p <= 0, 2^32 if p >= 1, else
+ *    llrintf(p * 2^32).  Recovery is unchanged.
  *
  * Uniforms (bit-plane contract): P_j = Philox4x32_10(key=(lo32(seed),hi32(seed)),
  * ctr=(a, t, r>>5, (tag<<8)|(j>>2)))[j&3] for j = 0..31, and bit (31-j) of u is bit
@@ -65,6 +74,7 @@
 #define TAG_LT_THRESH 4u
 #define TAG_LATENT 5u
 #define TAG_WEAKEN 6u
+#define TAG_ARC_INFECT 7u
 
 /* node states (= compartment index).  SIR/SIS: 0=S 1=I 2=R.  IC/LT: 0=inactive 1=newly
  * active (frontier) 2=active since an earlier step.  SI: 0=S 1=I.  SEIR/SEIS: 0=S 1=E
@@ -183,7 +193,30 @@ typedef struct {
     uint64_t g_rec;
     uint64_t p_const;
     uint64_t a_lat;       /* SEIR/SEIS latent threshold */
+    const float *arc_w;   /* optional [nnz] arc weights (SIR/SIS/SI): per-arc infection */
+    float beta_f;         /* beta in single precision (weighted threshold) */
 } orc_job;
+
+/* Weighted infection threshold of one arc (single precision, see the header). */
+static uint64_t arc_threshold(float beta_f, float w)
+{
+    const float p = beta_f * w;
+    if (!(p > 0.0f)) return 0;
+    if (p >= 1.0f) return 4294967296ull;
+    return (uint64_t)llrintf(p * 4294967296.0f);
+}
+
+/* Weighted infection of a susceptible node: some infectious in-arc transmits. */
+static int weighted_infected(const orc_job *jb, const uint8_t *X, int32_t beg, int32_t end,
+                             uint8_t infectious, uint32_t t, uint32_t r)
+{
+    for (int32_t e = beg; e < end; ++e) {
+        if (X[jb->col_idx[e]] != infectious) continue;
+        uint32_t u = orc_uniform(jb->rng_seed, TAG_ARC_INFECT, (uint32_t)e, t, r);
+        if ((uint64_t)u < arc_threshold(jb->beta_f, jb->arc_w[e])) return 1;
+    }
+    return 0;
+}
 
 typedef struct {
     orc_job *job;
@@ -202,6 +235,7 @@ static uint8_t node_update(const orc_job *jb, const uint8_t *X, int32_t v, uint3
     switch (jb->model) {
     case ORC_SIR:
     case ORC_SIS: {
+        if (s == ST_0 && jb->arc_w) return weighted_infected(jb, X, beg, end, ST_1, t, r) ? ST_1 : ST_0;
         if (s == ST_0) {
             int64_t k = 0;
             for (int32_t e = beg; e < end; ++e)
@@ -243,6 +277,7 @@ static uint8_t node_update(const orc_job *jb, const uint8_t *X, int32_t v, uint3
     }
     case ORC_SI: {
         if (s != ST_0) return s;
+        if (jb->arc_w) return weighted_infected(jb, X, beg, end, ST_1, t, r) ? ST_1 : ST_0;
         int64_t k = 0;
         for (int32_t e = beg; e < end; ++e)
             if (X[jb->col_idx[e]] == ST_1) ++k;
@@ -364,16 +399,19 @@ static void *worker_main(void *arg)
  * n_real*(T+1)*C u32, freq (optional) C*n u32, final_state (optional) n_real*n u8,
  * quiet_step (optional) n_real i32.
  */
-int orc_simulate_ext(int model, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
-                     double beta, double gamma, int ic_mode, double ic_p,
-                     double alpha, double mu, double nu,
-                     const int32_t *seeds, int64_t n_seeds, int32_t T, uint64_t rng_seed,
-                     const uint8_t *init_state, int32_t t0,
-                     int32_t r_lo, int32_t n_real, int nthreads,
-                     uint64_t *counts, uint32_t *per_real, uint32_t *freq, uint8_t *final_state,
-                     int32_t *quiet_step)
+/* As orc_simulate_ext, with optional arc weights (SIR, SIS and SI only; NULL =
+ * unweighted). */
+int orc_simulate_w(int model, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                   double beta, double gamma, int ic_mode, double ic_p,
+                   double alpha, double mu, double nu, const float *arc_w,
+                   const int32_t *seeds, int64_t n_seeds, int32_t T, uint64_t rng_seed,
+                   const uint8_t *init_state, int32_t t0,
+                   int32_t r_lo, int32_t n_real, int nthreads,
+                   uint64_t *counts, uint32_t *per_real, uint32_t *freq, uint8_t *final_state,
+                   int32_t *quiet_step)
 {
     if (model < 0 || model > 7 || n < 0 || T < 0 || n_real < 0 || r_lo < 0 || !counts) return -1;
+    if (arc_w && model != ORC_SIR && model != ORC_SIS && model != ORC_SI) return -1;
     if (nthreads < 1) nthreads = 1;
     for (int64_t i = 0; i < n_seeds; ++i)
         if (seeds[i] < 0 || seeds[i] >= n) return -1;
@@ -387,6 +425,11 @@ int orc_simulate_ext(int model, int32_t n, const int32_t *row_ptr, const int32_t
     jb.r_lo = r_lo; jb.n_real = n_real;
     jb.counts = counts; jb.per_real = per_real; jb.freq = freq; jb.final_state = final_state;
     jb.quiet_step = quiet_step;
+    jb.arc_w = arc_w;
+    jb.beta_f = (float)beta;
+    if (arc_w)
+        for (int64_t e = 0; e < (int64_t)row_ptr[n]; ++e)
+            if (!(arc_w[e] >= 0.0f) || arc_w[e] > 3.4e38f) return -1;   /* finite, >= 0 */
     int64_t maxdeg = 0;
     for (int32_t v = 0; v < n; ++v) {
         int64_t d = (int64_t)row_ptr[v + 1] - row_ptr[v];
@@ -432,6 +475,20 @@ int orc_simulate_ext(int model, int32_t n, const int32_t *row_ptr, const int32_t
     for (int i = 0; i < nthreads; ++i) { free(ws[i].counts); free(ws[i].freq); }
     free(ws); free(th); free(jb.surv); free(jb.surv_mu); free(jb.surv_nu);
     return rc;
+}
+
+int orc_simulate_ext(int model, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                     double beta, double gamma, int ic_mode, double ic_p,
+                     double alpha, double mu, double nu,
+                     const int32_t *seeds, int64_t n_seeds, int32_t T, uint64_t rng_seed,
+                     const uint8_t *init_state, int32_t t0,
+                     int32_t r_lo, int32_t n_real, int nthreads,
+                     uint64_t *counts, uint32_t *per_real, uint32_t *freq, uint8_t *final_state,
+                     int32_t *quiet_step)
+{
+    return orc_simulate_w(model, n, row_ptr, col_idx, beta, gamma, ic_mode, ic_p, alpha, mu, nu, NULL,
+                          seeds, n_seeds, T, rng_seed, init_state, t0, r_lo, n_real, nthreads,
+                          counts, per_real, freq, final_state, quiet_step);
 }
 
 /* The four models of the first table rows (SIR, SIS, IC, LT): three compartments. */
