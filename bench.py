@@ -438,6 +438,54 @@ def run_step_bench(args):
             "R": R, "peak_GBps": peak, "peak_source": peak_kind, "models": res}
 
 
+def run_weighted_bench(args):
+    """Weighted graphs: full Monte Carlo SIR on the R-MAT graph of --scale (default 26),
+    arc weights w_e ~ U[0, 2) (mean 1, seeded), beta = 0.01, gamma = 0.05, the benchmark's
+    seeds, R = 256, T = 100; each infectious in-arc transmits with probability beta * w_e.
+    One bench step = one full run.  The roofline unit is the dense step, whose bytes add
+    the 4-byte weight of every arc to the unweighted step's."""
+    import numpy as np
+    import torch
+    from paper_2603_14895_gb300 import fsgp
+    torch.cuda.set_device(0)
+    g, seeds = build_workload(args.scale)
+    w = np.random.default_rng(12345 + 7).uniform(0.0, 2.0, size=g.nnz).astype(np.float32)
+    graph = fsgp.Graph(g.row_ptr, g.col_idx)
+    graph.set_arc_weights(w)
+    stream = torch.cuda.current_stream()
+    out = fsgp.simulate(graph, fsgp.SIR, [seeds], R, T, RNG_SEED, beta=BETA, gamma=GAMMA, weighted=True)
+    for _ in range(args.warmup):
+        fsgp.simulate(graph, fsgp.SIR, [seeds], R, T, RNG_SEED, beta=BETA, gamma=GAMMA, weighted=True, out=out)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_selector(torch))
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        fsgp.simulate(graph, fsgp.SIR, [seeds], R, T, RNG_SEED, beta=BETA, gamma=GAMMA, weighted=True, out=out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    peak, peak_kind = measured_peaks()
+    b = step_bytes(g.n, g.nnz, R, 2) + 4.0 * g.nnz
+    achieved = T * b / (ms / 1e3) / 1e9
+    final = out["counts"][0, -1].cpu().tolist()
+    graph.close()
+    return {"metric": "edge-realization-steps/sec", "value": float(g.nnz) * R * T / (ms / 1e3),
+            "unit": "edge-realization-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"rmat{args.scale}_sir_weighted_R{R}_T{T}", "n": g.n, "nnz": g.nnz,
+                       "weights": "U[0, 2) per arc, seed 12352", "beta": BETA, "gamma": GAMMA,
+                       "seeds": int(len(seeds)), "final_SIR": final,
+                       "l2": "inputs larger than L2; no flush"},
+            "roofline": {"bound": "hbm", "kernel": "dense propagation step (all row launches of a step)",
+                         "achieved": achieved, "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "alg_bytes_per_step": b},
+            "clocks": clocks}
+
+
 # -------------------------------------------------------------- learned surrogate
 
 SG_R, SG_T, SG_GAMMA, SG_K = 1024, 100, 0.1, 20
@@ -720,7 +768,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="rmat26",
-                    choices=["rmat26", "batch", "surrogate", "ba1m", "er10k", "step", "screen"])
+                    choices=["rmat26", "batch", "surrogate", "ba1m", "er10k", "step", "screen", "weighted"])
     ap.add_argument("--screen-n", type=int, default=500_000)
     ap.add_argument("--t-mid", type=int, default=50)
     ap.add_argument("--sg-graphs", type=int, default=200)
@@ -753,6 +801,9 @@ def main():
         return
     if args.workload == "surrogate" and args.impl == "fsgp":
         print(json.dumps(run_surrogate_bench(args)), flush=True)
+        return
+    if args.workload == "weighted" and args.impl == "fsgp":
+        print(json.dumps(run_weighted_bench(args)), flush=True)
         return
     if args.workload == "screen" and args.impl == "fsgp":
         print(json.dumps(run_screen_bench(args)), flush=True)

@@ -105,6 +105,14 @@ typedef struct {
     double alpha;     /* SEIR/SEIS: exposed -> infectious probability per step, [0, 1] */
     double mu;        /* SWIR: per-arc weakening probability, [0, 1] */
     double nu;        /* SWIR: per-arc infection probability of a weakened node, [0, 1] */
+    int32_t weighted; /* SIR, SIS, SI: 1 = weighted graph (Table 1's edge weights): each
+                         infectious in-arc e transmits independently with probability
+                         beta * w_e per step (w from fsgp_graph_set_arc_weights), drawn per
+                         arc (tag 7, keyed by e's position in col_idx, the step and the
+                         realization): u < thr_e with p = (float)beta * w_e in single
+                         precision, thr_e = 0 if p <= 0, 2^32 if p >= 1, else
+                         round(p * 2^32).  0 = the unweighted rule.  Not supported by
+                         fsgp_simulate_single and fsgp_step_noalloc (EUNSUPPORTED). */
 } fsgp_params;
 
 /* Optional per-kernel profile of one fsgp_simulate call (host struct).  Device times
@@ -199,6 +207,14 @@ int fsgp_graph_destroy(fsgp_graph *g);
  * the next run allocates it again.  Useful when many graphs stay alive.  Synchronises
  * the device.  Errors: EINVAL (NULL), ECUDA. */
 int fsgp_graph_trim(fsgp_graph *g);
+
+/* Attach per-arc weights to graph g for weighted runs (fsgp_params.weighted): w[e] is
+ * the weight of arc e of the col_idx given to fsgp_graph_create (the caller's arc
+ * order), finite and >= 0; flags says whether w is host or device memory.  The graph
+ * keeps a device copy (4 bytes per arc) until it is destroyed or w is NULL (detach).
+ * Synchronises `stream`.  Errors: EINVAL (a weight negative, NaN or infinite: nothing
+ * changes), ENOMEM, ECUDA. */
+int fsgp_graph_set_arc_weights(fsgp_graph *g, const float *w, uint32_t flags, void *stream);
 
 /* Query sizes: any output pointer may be NULL. */
 int fsgp_graph_info(const fsgp_graph *g, int32_t *n, int64_t *nnz, int32_t *max_in_degree,

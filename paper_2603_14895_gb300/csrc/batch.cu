@@ -65,7 +65,7 @@ int probe(fsgp_graph *g, int model, const fsgp_params *p, const int32_t *seeds, 
     FSGP_CUDA(cudaEventCreate(&a));
     FSGP_CUDA(cudaEventCreate(&b));
     cudaEventRecord(a, s);
-    int rc = run_sets(g, model == FSGP_SI ? FSGP_SIS : model, p->ic_mode, &x, 1, T, opt, s);
+    int rc = run_sets(g, model == FSGP_SI ? FSGP_SIS : model, p->ic_mode, p->weighted ? 1 : 0, &x, 1, T, opt, s);
     cudaEventRecord(b, s);
     cudaError_t e = cudaEventSynchronize(b);
     if (rc == FSGP_OK && e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
@@ -168,14 +168,15 @@ extern "C" int fsgp_batch_run(const fsgp_request *reqs, int32_t n, const fsgp_ba
     if (n == 0) return FSGP_OK;
     cudaStream_t caller = (cudaStream_t)stream;
 
-    // groups: (graph, model, ic_mode, T) -> requests
-    using Key = std::tuple<const fsgp_graph *, int, int, int>;
+    // groups: (graph, model, ic_mode, T, weighted) -> requests
+    using Key = std::tuple<const fsgp_graph *, int, int, int, int>;
     std::map<Key, std::vector<int>> groups;
     std::map<const fsgp_graph *, double> cost;
     for (int i = 0; i < n; ++i) {
         const fsgp_request &q = reqs[i];
         // SI runs as SIS without recovery
-        groups[Key(q.graph, q.model == FSGP_SI ? FSGP_SIS : q.model, q.params.ic_mode, q.T)].push_back(i);
+        groups[Key(q.graph, q.model == FSGP_SI ? FSGP_SIS : q.model, q.params.ic_mode, q.T,
+                   q.params.weighted ? 1 : 0)].push_back(i);
         cost[q.graph] += (double)(q.graph->nnz + q.graph->n) * q.R * std::max(q.T, 1);
     }
     // per-graph tuning (optional): one probe series on the graph's first request
@@ -266,7 +267,7 @@ extern "C" int fsgp_batch_run(const fsgp_request *reqs, int32_t n, const fsgp_ba
                     x.steps_run = q.result.steps_run;
                     x.out_flags = FSGP_PTR_DEVICE;
                 }
-                const int rc = run_sets(const_cast<fsgp_graph *>(g), std::get<1>(key), std::get<2>(key),
+                const int rc = run_sets(const_cast<fsgp_graph *>(g), std::get<1>(key), std::get<2>(key), std::get<4>(key),
                                         specs.data(), (int)specs.size(), std::get<3>(key), tuned.at(g), st);
                 if (rc) {
                     rcs[k] = rc;

@@ -19,6 +19,13 @@ constexpr uint32_t TAG_IC_EDGE = 3u;
 constexpr uint32_t TAG_LT_THRESH = 4u;
 constexpr uint32_t TAG_LATENT = 5u;
 constexpr uint32_t TAG_WEAKEN = 6u;
+constexpr uint32_t TAG_ARC_INFECT = 7u;
+
+// Row-kernel models of weighted graphs (not public model numbers: a run of FSGP_SIR or
+// FSGP_SIS with fsgp_params.weighted set takes these kernels): an infectious in-arc e
+// transmits with probability beta * w_e, drawn per arc like an IC arc.
+constexpr int kSirW = 8;
+constexpr int kSisW = 9;
 constexpr uint64_t TWO32 = 4294967296ull;
 
 constexpr int kBlock = 256;          // threads per CTA for the row kernels
@@ -156,6 +163,7 @@ struct fsgp_graph {
     fsgp::HubTable hub{};
     fsgp::Workspace ws{};
     std::vector<fsgp::ExecCache> execs;   // most recent last (they point into ws)
+    float *arc_w = nullptr;         // [nnz] arc weights in the caller's arc order, or null
     fsgp::SgCache sgc{};
     int tuned = 0;                  // fsgp_batch_run: tuning chosen by an autotuned call
     fsgp_options tuned_opt{};

@@ -6,6 +6,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -298,6 +299,7 @@ static void release(fsgp_graph *g) {
     cudaFree(g->col2);
     cudaFree(g->arc0);
     cudaFree(g->lane_tab);
+    cudaFree(g->arc_w);
     cudaFree(g->hub.d_chunk_base);
     cudaFree(g->ws.ptr);
     cudaFree(g->sgc.inv_din);
@@ -527,6 +529,63 @@ extern "C" int fsgp_graph_destroy(fsgp_graph *g) {
     cudaDeviceSynchronize();
     release(g);
     cudaSetDevice(dev);
+    return FSGP_OK;
+}
+
+// Weights of a device array: flag a negative, NaN or infinite one.
+__global__ void k_check_weights(const float *w, int64_t n, int32_t *bad) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = w[i];
+        if (!(x >= 0.0f) || isinf(x)) atomicExch(bad, 1);
+    }
+}
+
+extern "C" int fsgp_graph_set_arc_weights(fsgp_graph *g, const float *w, uint32_t flags, void *stream) {
+    set_error("");
+    if (!g) return fail(FSGP_EINVAL, "graph is NULL");
+    if (flags != FSGP_PTR_HOST && flags != FSGP_PTR_DEVICE) return fail(FSGP_EINVAL, "bad weight flags");
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0;
+    FSGP_CUDA(cudaGetDevice(&dev));
+    if (dev != g->device) return fail(FSGP_EINVAL, "current device differs from the graph's device");
+    if (!w) {   // detach
+        FSGP_CUDA(cudaStreamSynchronize(s));
+        drop_exec_cache(g);
+        cudaFree(g->arc_w);
+        g->arc_w = nullptr;
+        return FSGP_OK;
+    }
+    const int64_t m = g->nnz;
+    if (flags == FSGP_PTR_HOST) {
+        for (int64_t i = 0; i < m; ++i)
+            if (!(w[i] >= 0.0f) || std::isinf(w[i])) return fail(FSGP_EINVAL, "arc weights must be finite and >= 0");
+    } else if (m > 0) {
+        int32_t *d_bad = nullptr, bad = 0;
+        FSGP_CUDA(cudaMalloc(&d_bad, sizeof(int32_t)));
+        cudaError_t e = cudaMemsetAsync(d_bad, 0, sizeof(int32_t), s);
+        if (e == cudaSuccess) {
+            const int grid = (int)std::min<int64_t>((m + 255) / 256, (int64_t)g->sm_count * 8);
+            k_check_weights<<<grid, 256, 0, s>>>(w, m, d_bad);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof bad, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(d_bad);
+        if (e != cudaSuccess) return cuda_fail(e, "arc weight check");
+        if (bad) return fail(FSGP_EINVAL, "arc weights must be finite and >= 0");
+    }
+    if (!g->arc_w) {
+        float *d = nullptr;
+        if (cudaMalloc(&d, sizeof(float) * (size_t)std::max<int64_t>(m, 1)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FSGP_ENOMEM, "device allocation of the arc weights failed");
+        }
+        g->arc_w = d;
+    }
+    if (m > 0)
+        FSGP_CUDA(cudaMemcpyAsync(g->arc_w, w, sizeof(float) * (size_t)m,
+                                  flags == FSGP_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    FSGP_CUDA(cudaStreamSynchronize(s));
     return FSGP_OK;
 }
 

@@ -176,6 +176,7 @@ extern "C" int fsgp_step_noalloc(int32_t model, const fsgp_params *params, const
     auto bad_p = [](double p) { return !(p >= 0.0 && p <= 1.0); };
     if (bad_p(params->beta) || bad_p(params->gamma) || bad_p(params->ic_p))
         return fail(FSGP_EINVAL, "probabilities must lie in [0, 1]");
+    if (params->weighted) return fail(FSGP_EUNSUPPORTED, "the no-allocation step has no weighted graphs");
     if (params->ic_mode != FSGP_IC_WEIGHTED_CASCADE && params->ic_mode != FSGP_IC_CONSTANT)
         return fail(FSGP_EINVAL, "bad ic_mode");
     const int W = (R + 31) / 32;

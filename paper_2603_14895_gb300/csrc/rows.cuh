@@ -70,10 +70,15 @@ __device__ __forceinline__ void st_vec(uint32_t *p, const uint32_t (&w)[V]) {
 template <int MODEL>
 struct ModelTraits {
     // SIR: I, R.  SIS: I.  IC, LT: A, F.  SEIR: I, R, E.  SEIS: I, E.  SWIR: I, R, W.
-    static constexpr int planes = MODEL == FSGP_SIS ? 1 : ((MODEL == FSGP_SEIR || MODEL == FSGP_SWIR) ? 3 : 2);
+    // Weighted SIR / SIS: as SIR / SIS.
+    static constexpr int planes = (MODEL == FSGP_SIS || MODEL == kSisW)
+                                      ? 1
+                                      : ((MODEL == FSGP_SEIR || MODEL == FSGP_SWIR) ? 3 : 2);
     // plane gathered from in-neighbours: I (epidemic models), F (IC), A (LT)
     static constexpr int src_plane = MODEL == FSGP_IC ? 1 : 0;
-    static constexpr bool counts = MODEL != FSGP_IC;
+    // per-arc draws (live-lane masks) instead of in-arc counts: IC and weighted graphs
+    static constexpr bool weighted = MODEL == kSirW || MODEL == kSisW;
+    static constexpr bool counts = MODEL != FSGP_IC && !weighted;
     // the state's source lanes are plane 1 (F) for IC / LT, plane 0 (I) otherwise
     static constexpr bool cascade = MODEL == FSGP_IC || MODEL == FSGP_LT;
     // hub rows may stop reading once every susceptible lane reaches K_sat
@@ -85,7 +90,8 @@ struct ModelTraits {
 // inactive lanes.
 template <int MODEL>
 __device__ __forceinline__ uint32_t need_of(uint32_t vm, uint32_t s0, uint32_t s1, uint32_t s2) {
-    if constexpr (MODEL == FSGP_SIR || MODEL == FSGP_SEIS || MODEL == FSGP_SWIR) return vm & ~s0 & ~s1;
+    if constexpr (MODEL == FSGP_SIR || MODEL == kSirW || MODEL == FSGP_SEIS || MODEL == FSGP_SWIR)
+        return vm & ~s0 & ~s1;
     else if constexpr (MODEL == FSGP_SEIR) return vm & ~s0 & ~s1 & ~s2;
     else return vm & ~s0;
 }
@@ -102,6 +108,15 @@ __device__ __forceinline__ WordOut update_word(const StepArgs &A, uint32_t node,
     } else if constexpr (MODEL == FSGP_IC) {
         o.n0 = s0 | newly;
         o.n1 = newly;
+        o.n2 = 0u;
+    } else if constexpr (ModelTraits<MODEL>::weighted) {
+        // infected: a susceptible lane some infectious in-arc transmitted to; recovery
+        // as in SIR / SIS
+        const uint32_t infect = newly & need_of<MODEL>(x.vm, s0, s1, 0u);
+        const uint32_t rec = lanes_u_less(s0 & x.vm, __ldg(&A.sp[x.s].g_rec), node, A.t, x.g, TAG_RECOVER,
+                                          x.k0, x.k1);
+        o.n0 = (s0 & ~rec) | infect;
+        o.n1 = MODEL == kSirW ? (s1 | rec) : 0u;
         o.n2 = 0u;
     } else if constexpr (MODEL == FSGP_LT) {
         o = update_lt_word<B>(A, node, x, s0, d, c);
@@ -175,9 +190,13 @@ __device__ __forceinline__ void gather_arcs(const StepArgs &A, int64_t e_begin, 
 #pragma unroll
                 for (int i = 0; i < V; ++i) {
                     const uint32_t m = xs[j].w[i] & need[i] & ~newly[i];
-                    if (m)
-                        newly[i] |= lanes_u_less(m, ic_thr[i], (uint32_t)(e + j + arcb), A.t, x[i].g,
-                                                 TAG_IC_EDGE, x[i].k0, x[i].k1);
+                    if (m) {
+                        constexpr bool W = ModelTraits<MODEL>::weighted;
+                        const int64_t ep = e + j + arcb;   // the caller's arc position
+                        const uint64_t thr = W ? arc_threshold(A, x[i].s, ep) : ic_thr[i];
+                        newly[i] |= lanes_u_less(m, thr, (uint32_t)ep, A.t, x[i].g, W ? TAG_ARC_INFECT : TAG_IC_EDGE,
+                                                 x[i].k0, x[i].k1);
+                    }
                 }
             }
         }
@@ -845,7 +864,7 @@ __global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
             node = (uint32_t)e.x;
             const int32_t u[kLaneMaxDeg] = {e.y, e.z, e.w};
             d = (e.y >= 0) + (e.z >= 0) + (e.w >= 0);
-            if (MODEL == FSGP_IC && d > 0) beg = __ldg(A.arc0 + v);   // arc positions key the draws
+            if (!ModelTraits<MODEL>::counts && d > 0) beg = __ldg(A.arc0 + v);   // arc positions key the draws
             const size_t off = (size_t)v * A.Wn + w0;
             // own words and sources' words, 4 (or fewer) words per load; `busy` records
             // whether any lane can change at this step (an infected lane to recover, or a
@@ -908,13 +927,16 @@ __global__ void __launch_bounds__(kBlock) k_rows_lane(StepArgs A) {
                 const uint32_t x0 = st.v[P][i][tid], x1 = st.v[P + 1][i][tid], x2 = st.v[P + 2][i][tid];
                 const uint32_t need = need_of<MODEL>(x.vm, s0, s1, s2);
                 uint32_t c[2] = {0u, 0u}, newly = 0u;
-                if constexpr (MODEL == FSGP_IC) {
-                    const uint64_t thr = ic_threshold(A, x.s, d);
+                if constexpr (!ModelTraits<MODEL>::counts) {
+                    constexpr bool W = ModelTraits<MODEL>::weighted;
+                    const uint64_t thr = W ? 0ull : ic_threshold(A, x.s, d);
                     const uint32_t xs[kLaneMaxDeg] = {x0, x1, x2};
 #pragma unroll
                     for (int j = 0; j < kLaneMaxDeg; ++j) {
                         const uint32_t m = xs[j] & need & ~newly;
-                        if (m) newly |= lanes_u_less(m, thr, (uint32_t)(beg + j), A.t, x.g, TAG_IC_EDGE, x.k0, x.k1);
+                        if (m)
+                            newly |= lanes_u_less(m, W ? arc_threshold(A, x.s, beg + j) : thr, (uint32_t)(beg + j),
+                                                  A.t, x.g, W ? TAG_ARC_INFECT : TAG_IC_EDGE, x.k0, x.k1);
                     }
                 } else {
                     // counts of set source lanes (at most 3): two bit-planes

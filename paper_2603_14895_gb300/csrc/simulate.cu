@@ -438,6 +438,8 @@ static int launch_rows_model(int model, const StepArgs &A, const StepLaunch &L, 
         case FSGP_SEIR: return launch_rows<FSGP_SEIR>(A, L, s);
         case FSGP_SEIS: return launch_rows<FSGP_SEIS>(A, L, s);
         case FSGP_SWIR: return launch_rows<FSGP_SWIR>(A, L, s);
+        case kSirW: return launch_rows<kSirW>(A, L, s);
+        case kSisW: return launch_rows<kSisW>(A, L, s);
         default: return fail(FSGP_EINVAL, "model without row kernels");
     }
 }
@@ -451,6 +453,8 @@ static int occupancy_model(int model, int V, int TEAM, size_t smem, RowOccupancy
         case FSGP_SEIR: return occupancy_rows<FSGP_SEIR>(V, TEAM, smem, o);
         case FSGP_SEIS: return occupancy_rows<FSGP_SEIS>(V, TEAM, smem, o);
         case FSGP_SWIR: return occupancy_rows<FSGP_SWIR>(V, TEAM, smem, o);
+        case kSirW: return occupancy_rows<kSirW>(V, TEAM, smem, o);
+        case kSisW: return occupancy_rows<kSisW>(V, TEAM, smem, o);
         default: return fail(FSGP_EINVAL, "model without row kernels");
     }
 }
@@ -465,6 +469,8 @@ static int launch_persist_model(int model, const StepArgs &A, const PersistArgs 
         case FSGP_SEIR: return launch_persist<FSGP_SEIR>(A, Q, TEAM, grid, smem, sm_count, s, grid_out);
         case FSGP_SEIS: return launch_persist<FSGP_SEIS>(A, Q, TEAM, grid, smem, sm_count, s, grid_out);
         case FSGP_SWIR: return launch_persist<FSGP_SWIR>(A, Q, TEAM, grid, smem, sm_count, s, grid_out);
+        case kSirW: return launch_persist<kSirW>(A, Q, TEAM, grid, smem, sm_count, s, grid_out);
+        case kSisW: return launch_persist<kSisW>(A, Q, TEAM, grid, smem, sm_count, s, grid_out);
         default: return fail(FSGP_EINVAL, "model without row kernels");
     }
 }
@@ -503,9 +509,11 @@ void survival_table(double beta, int32_t max_deg, std::vector<uint64_t> &out, in
 }
 
 // One launch sequence over S sets that share Ws.
-static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const *sets, int S,
+static int run_wave(fsgp_graph *g, int model, int ic_mode, int weighted, const SetSpec *const *sets, int S,
                     int Ws, int T, const fsgp_options &opt, cudaStream_t s) {
     const int32_t n = g->n;
+    // the row kernels' model: weighted graphs draw per arc (SIR and SIS only)
+    const int kmodel = weighted ? (model == FSGP_SIR ? kSirW : kSisW) : model;
     const int P = fsgp_model_planes(model);
     const int C = n_compartments(model);
     const int Wn = S * Ws;
@@ -608,6 +616,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
         p.last_mask = (x.R & 31) ? ((1u << (x.R & 31)) - 1u) : 0xffffffffu;
         p.R = x.R;
         p.g_rec = (uint64_t)llrint(x.gamma * 4294967296.0);
+        p.beta_f = (float)x.beta;
         p.p_const = (uint64_t)llrint(x.ic_p * 4294967296.0);
         seed_off[i] = seeds_total;
         if (!x.init_planes && x.seed_flags == FSGP_PTR_HOST) seeds_total += x.n_seeds;
@@ -644,7 +653,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     sz[O_OUT] = (size_t)S * sizeof(SetOut);
     sz[O_STEPS] = (size_t)S * sizeof(int32_t);
     sz[O_D0] = (size_t)n_d0 * sizeof(int32_t);
-    const bool hub_sat = model == FSGP_SIR || model == FSGP_SIS || model == FSGP_SEIR || model == FSGP_SEIS;
+    const bool hub_sat = !weighted && (model == FSGP_SIR || model == FSGP_SIS || model == FSGP_SEIR || model == FSGP_SEIS);
     sz[O_HUBSAT] = hub_sat ? (size_t)n_hubs * nslices * sizeof(uint32_t) : 0;
     size_t off[O_END], total = 0;
     for (int i = 0; i < O_END; ++i) {
@@ -697,7 +706,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     if (smem_lanes > 32 * 1024) return fail(FSGP_EINVAL, "per-lane counters exceed shared memory");
     RowOccupancy occ{};
     occ.swl = lane_swl;
-    rc = occupancy_model(model, V, TEAM, smem_lanes, &occ);
+    rc = occupancy_model(kmodel, V, TEAM, smem_lanes, &occ);
     if (rc) return rc;
     Prof prof;
     const bool profiling = opt.profile != nullptr;
@@ -787,6 +796,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     A.hub_scratch = hub_scratch;
     A.hub_sat = (hub_sat && n_hubs > 0) ? (uint32_t *)(ws + off[O_HUBSAT]) : nullptr;
     A.prof_bytes = profiling ? d_prof : nullptr;
+    A.arc_w = weighted ? g->arc_w : nullptr;
 
     FSGP_CUDA(cudaMemsetAsync(ws + off[O_STATE], 0, sz[O_STATE], s));
     FSGP_CUDA(cudaMemsetAsync(pc, 0, sz[O_PC], s));
@@ -854,7 +864,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
         auto put = [&sig](const void *p, size_t b) {
             sig.insert(sig.end(), (const uint8_t *)p, (const uint8_t *)p + b);
         };
-        const int flags[6] = {model, T, allow_sparse ? 1 : 0, any_init ? 1 : 0, want_lanes ? 1 : 0,
+        const int flags[6] = {kmodel, T, allow_sparse ? 1 : 0, any_init ? 1 : 0, want_lanes ? 1 : 0,
                               want_freq ? 1 : 0};
         put(flags, sizeof flags);
         put(&sparse_limit, sizeof sparse_limit);
@@ -888,7 +898,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
         Q.t0 = (uint32_t)opt.t0;
         Q.spin_limit = kPersistSpinCycles;
         int grid_used = 0;
-        rc = launch_persist_model(model, A, Q, TEAM, L.grid_small, L.smem_lanes, g->sm_count, s, &grid_used);
+        rc = launch_persist_model(kmodel, A, Q, TEAM, L.grid_small, L.smem_lanes, g->sm_count, s, &grid_used);
         if (rc == FSGP_OK) {
             const int width = S * kPC;
             k_pc_prefix<<<(width + 255) / 256, 256, 0, s>>>(pc, (int)T, width);
@@ -916,7 +926,7 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
             k_mark<<<grid_mark, kBlock, 0, s>>>(A);
             if (profiling) prof.stop(s);
         }
-        rc = launch_rows_model(model, A, L, s);
+        rc = launch_rows_model(kmodel, A, L, s);
         if (rc) return rc;
         launches += 1 + (allow_sparse ? 1 : 0) + (L.have_hub ? (A.hub_sat ? 3 : 2) : 0) + (L.have_mid ? 1 : 0) +
                     (L.have_small ? 1 : 0) + (L.have_small4 ? 1 : 0) + (L.have_lane ? 1 : 0);
@@ -1014,9 +1024,14 @@ static int run_wave(fsgp_graph *g, int model, int ic_mode, const SetSpec *const 
     return FSGP_OK;
 }
 
-int run_sets(fsgp_graph *g, int model, int ic_mode, const SetSpec *sets, int n_sets, int T,
+int run_sets(fsgp_graph *g, int model, int ic_mode, int weighted, const SetSpec *sets, int n_sets, int T,
              const fsgp_options &opt, cudaStream_t s) {
     if (n_sets < 1) return FSGP_OK;
+    if (weighted) {
+        if (model != FSGP_SIR && model != FSGP_SIS)
+            return fail(FSGP_EINVAL, "weighted graphs: SIR, SIS or SI only");
+        if (!g->arc_w) return fail(FSGP_EINVAL, "weighted run on a graph without arc weights");
+    }
     const uint32_t of = sets[0].out_flags;
     for (int i = 0; i < n_sets; ++i) {
         const SetSpec &x = sets[i];
@@ -1066,7 +1081,7 @@ int run_sets(fsgp_graph *g, int model, int ic_mode, const SetSpec *sets, int n_s
             wave.push_back(x);
             ++i;
         }
-        const int rc = run_wave(g, model, ic_mode, wave.data(), (int)wave.size(), Ws, T, opt, s);
+        const int rc = run_wave(g, model, ic_mode, weighted, wave.data(), (int)wave.size(), Ws, T, opt, s);
         if (rc) return rc;
     }
     return FSGP_OK;
@@ -1144,7 +1159,8 @@ extern "C" int fsgp_simulate(const fsgp_graph *gc, int32_t model, const fsgp_par
         x.steps_run = out->steps_run ? out->steps_run + i : nullptr;
         x.out_flags = out->flags;
     }
-    return run_sets(g, run_model, params->ic_mode, sets.data(), n_sets, T, opt, (cudaStream_t)stream);
+    return run_sets(g, run_model, params->ic_mode, params->weighted ? 1 : 0, sets.data(), n_sets, T, opt,
+                    (cudaStream_t)stream);
 }
 
 extern "C" int fsgp_selftest_barrier(int32_t ctas, int32_t missing, int32_t rounds, int64_t spin_cycles,

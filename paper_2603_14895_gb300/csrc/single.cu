@@ -242,6 +242,7 @@ extern "C" int fsgp_simulate_single(const fsgp_graph *gc, int32_t model, const f
     if (!(params->beta >= 0.0 && params->beta <= 1.0 && params->gamma >= 0.0 && params->gamma <= 1.0 &&
           params->ic_p >= 0.0 && params->ic_p <= 1.0))
         return fail(FSGP_EINVAL, "probability outside [0, 1]");
+    if (params->weighted) return fail(FSGP_EUNSUPPORTED, "the single-instance path has no weighted graphs");
     if (params->ic_mode != FSGP_IC_WEIGHTED_CASCADE && params->ic_mode != FSGP_IC_CONSTANT)
         return fail(FSGP_EINVAL, "unknown ic_mode");
     cudaStream_t st = (cudaStream_t)stream;

@@ -73,6 +73,7 @@ struct SetParams {
     int32_t ksat_mu;
     const uint64_t *surv_nu;        // SWIR: survival table of weakened lanes, and its K_sat
     int32_t ksat_nu;
+    float beta_f;                   // weighted graphs: beta in single precision
 };
 
 // Running plane popcounts are kept for up to three planes per set.
@@ -135,7 +136,18 @@ struct StepArgs {
     uint32_t *hub_sat;              // SIR/SIS: [n_hubs][nslices] the slice's susceptible lanes
                                     // all reached K_sat within the row's first chunk, or null
     unsigned long long *prof_bytes; // [FSGP_PROF_KINDS] algorithmic bytes per kind, or null
+    const float *__restrict__ arc_w; // weighted graphs: [nnz] weights in the caller's arc order
 };
+
+// Weighted graphs: transmission threshold of the arc at caller position epos for a lane
+// of set s.  p = beta * w_e in single precision; 0 if p <= 0, 2^32 (certain) if p >= 1,
+// else round(p * 2^32) (the scaling by 2^32 is exact).
+__device__ __forceinline__ uint64_t arc_threshold(const StepArgs &A, int s, int64_t epos) {
+    const float p = __fmul_rn(__ldg(&A.sp[s].beta_f), __ldg(A.arc_w + epos));
+    if (!(p > 0.0f)) return 0ull;
+    if (p >= 1.0f) return TWO32;
+    return (uint64_t)__float2ull_rn(__fmul_rn(p, 4294967296.0f));
+}
 
 // Node (Philox subject) of new row i, and new row of node v.
 __device__ __forceinline__ uint32_t node_of(const StepArgs &A, int32_t i) {
@@ -717,7 +729,8 @@ struct SetSpec {
 
 // Runs every set for T steps on graph g (simulate.cu).  Sets with the same words per
 // set run side by side in one launch sequence (up to kMaxSets at a time).
-int run_sets(fsgp_graph *g, int model, int ic_mode, const SetSpec *sets, int n_sets, int T,
+// weighted: SIR / SIS on the graph's arc weights (per-arc transmission draws).
+int run_sets(fsgp_graph *g, int model, int ic_mode, int weighted, const SetSpec *sets, int n_sets, int T,
              const fsgp_options &opt, cudaStream_t s);
 
 template <int MODEL>

@@ -34,7 +34,8 @@ class FsgpError(RuntimeError):
 class fsgp_params(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("ic_mode", ctypes.c_int32), ("ic_p", ctypes.c_double),
-                ("alpha", ctypes.c_double), ("mu", ctypes.c_double), ("nu", ctypes.c_double)]
+                ("alpha", ctypes.c_double), ("mu", ctypes.c_double), ("nu", ctypes.c_double),
+                ("weighted", ctypes.c_int32)]
 
 
 PROF_KINDS = 10
@@ -147,6 +148,8 @@ def load():
         lib.fsgp_surrogate_screen.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_double, ctypes.c_double, P, P]
         lib.fsgp_surrogate_screen.restype = ctypes.c_int
+        lib.fsgp_graph_set_arc_weights.argtypes = [P, P, ctypes.c_uint32, P]
+        lib.fsgp_graph_set_arc_weights.restype = ctypes.c_int
         lib.fsgp_selftest_barrier.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, P]
         lib.fsgp_selftest_barrier.restype = ctypes.c_int
         lib.fsgp_last_error.argtypes = []
@@ -249,6 +252,21 @@ def fsgp_step_noalloc(model, params: fsgp_params, row_ptr, col_idx, n, nnz, R, t
                                     _stream_handle(stream)))
 
 
+def fsgp_graph_set_arc_weights(h, w, stream=None) -> None:
+    if w is None:
+        _check(load().fsgp_graph_set_arc_weights(h, None, PTR_HOST, _stream_handle(stream)))
+        return
+    if isinstance(w, np.ndarray):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        flags = PTR_HOST
+    else:
+        import torch
+        assert w.dtype == torch.float32
+        w = w.contiguous()
+        flags = PTR_DEVICE if w.is_cuda else PTR_HOST
+    _check(load().fsgp_graph_set_arc_weights(h, _ptr(w), flags, _stream_handle(stream)))
+
+
 def fsgp_selftest_barrier(ctas: int, missing: int, rounds: int, spin_cycles: int, stream=None) -> int:
     """Status of the grid-barrier self-test (FSGP_OK or FSGP_ETIMEOUT; other codes raise)."""
     rc = load().fsgp_selftest_barrier(ctas, missing, rounds, ctypes.c_int64(spin_cycles),
@@ -298,6 +316,11 @@ class Graph:
         """Free the cached simulation workspace (fsgp_graph_trim)."""
         fsgp_graph_trim(self.handle)
 
+    def set_arc_weights(self, w, stream=None) -> None:
+        """Per-arc weights (float32, the caller's arc order) for weighted runs; None
+        detaches them (fsgp_graph_set_arc_weights)."""
+        fsgp_graph_set_arc_weights(self.handle, w, stream)
+
     def close(self):
         if getattr(self, "handle", None) is not None:
             fsgp_graph_destroy(self.handle)
@@ -324,10 +347,11 @@ def make_options(**kw) -> fsgp_options:
 
 def simulate(graph: Graph, model: int, seed_sets, R: int, T: int, rng_seed: int, *, beta=0.0,
              gamma=0.0, ic_mode=IC_WEIGHTED_CASCADE, ic_p=0.0, alpha=0.0, mu=0.0, nu=0.0,
-             freq=True, per_real=False, final_planes=False, steps_run=True, device=True,
+             weighted=False, freq=True, per_real=False, final_planes=False, steps_run=True, device=True,
              options=None, stream=None, out=None):
     """Run fsgp_simulate; results are torch tensors on the current CUDA device
-    (device=True) or numpy arrays (device=False)."""
+    (device=True) or numpy arrays (device=False).  weighted: SIR/SIS/SI on the graph's
+    arc weights (Graph.set_arc_weights)."""
     import torch
     n = graph.n
     if isinstance(seed_sets, np.ndarray) and seed_sets.ndim == 1:
@@ -373,7 +397,8 @@ def simulate(graph: Graph, model: int, seed_sets, R: int, T: int, rng_seed: int,
     res.per_real = _ptr(out.get("per_real"))
     res.final_planes = _ptr(out.get("final_planes"))
     res.steps_run = _ptr(out.get("steps_run"))
-    prm = fsgp_params(beta=beta, gamma=gamma, ic_mode=ic_mode, ic_p=ic_p, alpha=alpha, mu=mu, nu=nu)
+    prm = fsgp_params(beta=beta, gamma=gamma, ic_mode=ic_mode, ic_p=ic_p, alpha=alpha, mu=mu, nu=nu,
+                      weighted=1 if weighted else 0)
     if isinstance(options, dict):
         options = make_options(**options)
     fsgp_simulate(graph.handle, model, prm, seeds, offs, n_sets, PTR_HOST, R, T, rng_seed,
@@ -382,16 +407,18 @@ def simulate(graph: Graph, model: int, seed_sets, R: int, T: int, rng_seed: int,
 
 
 def simulate_single(graph: Graph, model: int, seeds, r: int, T: int, rng_seed: int, *, beta=0.0,
-                    gamma=0.0, ic_mode=IC_WEIGHTED_CASCADE, ic_p=0.0, final_state=True, stream=None):
+                    gamma=0.0, ic_mode=IC_WEIGHTED_CASCADE, ic_p=0.0, weighted=False, final_state=True,
+                    stream=None):
     """The plain single-instance path (fsgp_simulate_single) for realization r; returns
-    device tensors counts [T+1][3] (int64), final_state [n] (uint8) and steps_run."""
+    device tensors counts [T+1][3] (int64), final_state [n] (uint8) and steps_run.
+    (weighted=True is rejected: the path has no weighted graphs.)"""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     seeds = np.ascontiguousarray(seeds, dtype=np.int32)
     counts = torch.zeros((T + 1, 3), dtype=torch.int64, device=dev)
     fs = torch.zeros(graph.n, dtype=torch.uint8, device=dev) if final_state else None
     sr = torch.zeros(1, dtype=torch.int32, device=dev)
-    prm = fsgp_params(beta=beta, gamma=gamma, ic_mode=ic_mode, ic_p=ic_p)
+    prm = fsgp_params(beta=beta, gamma=gamma, ic_mode=ic_mode, ic_p=ic_p, weighted=1 if weighted else 0)
     _check(load().fsgp_simulate_single(graph.handle, model, ctypes.byref(prm),
                                        seeds.ctypes.data if seeds.size else None, seeds.size, PTR_HOST,
                                        r, T, rng_seed, _ptr(counts), _ptr(fs), _ptr(sr), PTR_DEVICE,
@@ -429,7 +456,8 @@ def batch_run(requests, *, n_streams=0, capture_graph=0, autotune=0, stream=None
         q.model = model
         q.params = fsgp_params(beta=rq.get("beta", 0.0), gamma=rq.get("gamma", 0.0),
                                ic_mode=rq.get("ic_mode", IC_WEIGHTED_CASCADE), ic_p=rq.get("ic_p", 0.0),
-                               alpha=rq.get("alpha", 0.0), mu=rq.get("mu", 0.0), nu=rq.get("nu", 0.0))
+                               alpha=rq.get("alpha", 0.0), mu=rq.get("mu", 0.0), nu=rq.get("nu", 0.0),
+                               weighted=1 if rq.get("weighted", False) else 0)
         q.seed_nodes = seeds.ctypes.data if seeds.size else None
         q.n_seeds = int(seeds.size)
         q.R, q.T, q.rng_seed = R, T, int(rq["rng_seed"])
