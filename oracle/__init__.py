@@ -82,6 +82,9 @@ def _load():
                 ctypes.c_uint64, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                 ctypes.c_int, P, P, P, P, P]
             lib.orc_simulate_w.restype = ctypes.c_int
+            lib.orc_hk.argtypes = [ctypes.c_int32, P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                   P, P, ctypes.c_int]
+            lib.orc_hk.restype = ctypes.c_int
             lib.orc_compartments.argtypes = [ctypes.c_int]
             lib.orc_compartments.restype = ctypes.c_int
             lib.orc_node_step.argtypes = [
@@ -190,3 +193,23 @@ def node_step(model: int, row_ptr, col_idx, v: int, X, *, beta=0.0, gamma=0.0,
     if s < 0:
         raise ValueError("orc_node_step failed")
     return s
+
+
+def hk(row_ptr, col_idx, h0, T: int, eps: float, nthreads=None):
+    """Hegselmann-Krause opinion dynamics (Appendix A.2) on the in-CSR graph: h0 is
+    [R][n] (float32, one opinion vector per realization); returns (h_T [R][n] float32,
+    changes [T+1] u64: (node, realization) pairs whose opinion changed at each step)."""
+    lib = _load()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    h0 = np.ascontiguousarray(np.atleast_2d(h0), dtype=np.float32)
+    R, n = h0.shape
+    assert n == row_ptr.shape[0] - 1
+    out = np.zeros_like(h0)
+    changes = np.zeros(T + 1, dtype=np.uint64)
+    rc = lib.orc_hk(n, _ptr(row_ptr), _ptr(col_idx), _ptr(h0), R, int(T), float(np.float32(eps)), _ptr(out),
+                    _ptr(changes), int(nthreads or os.cpu_count() or 1))
+    if rc != 0:
+        raise ValueError(f"orc_hk failed with code {rc}")
+    return out, changes
+

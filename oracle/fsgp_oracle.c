@@ -529,3 +529,93 @@ int orc_node_step(int model, const int32_t *row_ptr, const int32_t *col_idx, int
     free(jb.surv);
     return s;
 }
+
+/* ---------------- Hegselmann-Krause opinion dynamics (Appendix A.2) ----------------
+ * Continuous opinions, no randomness: R independent opinion vectors (realizations)
+ * given by the caller.  At step k every node i takes the mean of the opinions of its
+ * in-neighbours j (Sec. 2 convention N(i) = N^-(i), arcs with multiplicity, i itself
+ * only through a self-loop) whose distance |h_i - h_j| is below eps; with no such
+ * neighbour the opinion stays (the NaN case of the appendix).  Readings: the strict
+ * "< eps" of the appendix's message definition (its prose says "<= eps"), and single
+ * precision throughout (the paper's tensors), with the sum taken in col_idx order and
+ * one division, so that an implementation that keeps that order reproduces it exactly.
+ */
+typedef struct {
+    int32_t n;
+    const int32_t *row_ptr, *col_idx;
+    const float *h0;      /* [R][n] */
+    int32_t R, T;
+    float eps;
+    float *h_out;         /* [R][n] */
+    uint64_t *changes;    /* [T+1]: (node, realization) pairs whose opinion changed at step k */
+    int tid, nthreads;
+    uint64_t *local;      /* thread-local [T+1] */
+} orc_hk_job;
+
+static void *hk_worker(void *arg)
+{
+    orc_hk_job *jb = (orc_hk_job *)arg;
+    const int32_t n = jb->n;
+    float *X = (float *)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    float *Y = (float *)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    for (int32_t r = jb->tid; r < jb->R; r += jb->nthreads) {
+        memcpy(X, jb->h0 + (size_t)r * n, sizeof(float) * (size_t)n);
+        for (int32_t k = 1; k <= jb->T; ++k) {
+            uint64_t ch = 0;
+            for (int32_t i = 0; i < n; ++i) {
+                const float hi = X[i];
+                float sum = 0.0f;
+                int32_t cnt = 0;
+                for (int32_t e = jb->row_ptr[i]; e < jb->row_ptr[i + 1]; ++e) {
+                    const float hj = X[jb->col_idx[e]];
+                    if (fabsf(hi - hj) < jb->eps) {
+                        sum = sum + hj;
+                        ++cnt;
+                    }
+                }
+                Y[i] = cnt > 0 ? sum / (float)cnt : hi;
+                if (Y[i] != hi) ++ch;
+            }
+            float *tmp = X; X = Y; Y = tmp;
+            jb->local[k] += ch;
+        }
+        memcpy(jb->h_out + (size_t)r * n, X, sizeof(float) * (size_t)n);
+    }
+    free(X);
+    free(Y);
+    return NULL;
+}
+
+/* Returns 0, -1 (bad arguments: eps negative or not finite, an opinion not finite), or
+ * -2 (allocation). */
+int orc_hk(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const float *h0, int32_t R, int32_t T,
+           float eps, float *h_out, uint64_t *changes, int nthreads)
+{
+    if (n < 0 || R < 0 || T < 0 || !h0 || !h_out || !changes) return -1;
+    if (!(eps >= 0.0f) || isinf(eps)) return -1;
+    for (int64_t i = 0; i < (int64_t)R * n; ++i)
+        if (!(h0[i] == h0[i]) || isinf(h0[i])) return -1;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > R && R > 0) nthreads = R;
+    memset(changes, 0, sizeof(uint64_t) * (size_t)(T + 1));
+    orc_hk_job *jobs = (orc_hk_job *)calloc((size_t)nthreads, sizeof(orc_hk_job));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!jobs || !th) { free(jobs); free(th); return -2; }
+    int rc = 0;
+    for (int i = 0; i < nthreads; ++i) {
+        jobs[i] = (orc_hk_job){n, row_ptr, col_idx, h0, R, T, eps, h_out, changes, i, nthreads, NULL};
+        jobs[i].local = (uint64_t *)calloc((size_t)T + 1, sizeof(uint64_t));
+        if (!jobs[i].local) rc = -2;
+    }
+    if (rc == 0) {
+        for (int i = 0; i < nthreads; ++i) pthread_create(&th[i], NULL, hk_worker, &jobs[i]);
+        for (int i = 0; i < nthreads; ++i) pthread_join(th[i], NULL);
+        for (int i = 0; i < nthreads; ++i)
+            for (int32_t k = 0; k <= T; ++k) changes[k] += jobs[i].local[k];
+    }
+    for (int i = 0; i < nthreads; ++i) free(jobs[i].local);
+    free(jobs);
+    free(th);
+    return rc;
+}
+
