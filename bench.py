@@ -486,6 +486,55 @@ def run_weighted_bench(args):
             "clocks": clocks}
 
 
+def run_hk_bench(args):
+    """Hegselmann-Krause opinion dynamics (Appendix A.2): BA n = 1,000,000, m = 5 (both
+    arc directions, about 10M arcs), R = 64 opinion vectors U[-1, 1] (seeded), eps = 0.25,
+    T = 30 steps.  One bench step = one full run from the same start opinions (device
+    buffers).  Units are arcs x realizations x steps.  The roofline unit is one step:
+    every arc's 32-lane source segments (4 B per realization), its column index once
+    per 32-lane group, the node's own opinions read and written."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2603_14895_gb300 import fsgp
+    torch.cuda.set_device(0)
+    g = W.ba1m_graph()
+    R_hk, T_hk, eps = 64, 30, 0.25
+    h0 = torch.from_numpy(np.random.default_rng(12345 + 8).uniform(-1.0, 1.0, size=(R_hk, g.n))
+                          .astype(np.float32)).cuda()
+    graph = fsgp.Graph(g.row_ptr, g.col_idx)
+    for _ in range(args.warmup):
+        h, ch = fsgp.hk(graph, h0, T_hk, eps)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_selector(torch))
+    sampler.start()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(1, args.steps)     # (--steps 100 times about 1.5 s)
+    ev0.record(stream)
+    for _ in range(reps):
+        h, ch = fsgp.hk(graph, h0, T_hk, eps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / reps
+    groups = (R_hk + 31) // 32
+    b = 4.0 * g.nnz * groups * 32 + 4.0 * g.nnz * groups + 8.0 * g.n * groups * 32 + 4.0 * (g.n + 1)
+    peak, peak_kind = measured_peaks()
+    achieved = T_hk * b / (ms / 1e3) / 1e9
+    return {"metric": "edge-realization-steps/sec", "value": float(g.nnz) * R_hk * T_hk / (ms / 1e3),
+            "unit": "edge-realization-steps/s", "n_gpus": 1, "steps": reps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "ba1m_hk_R64_T30_eps0.25", "n": g.n, "nnz": g.nnz,
+                       "changes_last_step": int(ch[-1].item()), "changes_first_step": int(ch[1].item()),
+                       "l2": "opinions 256 MB per buffer, above L2; no flush"},
+            "roofline": {"bound": "hbm", "kernel": "k_hk_step (one step)", "achieved": achieved, "peak": peak,
+                         "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "alg_bytes_per_step": b},
+            "clocks": clocks}
+
+
 # -------------------------------------------------------------- learned surrogate
 
 SG_R, SG_T, SG_GAMMA, SG_K = 1024, 100, 0.1, 20
@@ -768,7 +817,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="rmat26",
-                    choices=["rmat26", "batch", "surrogate", "ba1m", "er10k", "step", "screen", "weighted"])
+                    choices=["rmat26", "batch", "surrogate", "ba1m", "er10k", "step", "screen", "weighted",
+                             "hk"])
     ap.add_argument("--screen-n", type=int, default=500_000)
     ap.add_argument("--t-mid", type=int, default=50)
     ap.add_argument("--sg-graphs", type=int, default=200)
@@ -801,6 +851,9 @@ def main():
         return
     if args.workload == "surrogate" and args.impl == "fsgp":
         print(json.dumps(run_surrogate_bench(args)), flush=True)
+        return
+    if args.workload == "hk" and args.impl == "fsgp":
+        print(json.dumps(run_hk_bench(args)), flush=True)
         return
     if args.workload == "weighted" and args.impl == "fsgp":
         print(json.dumps(run_weighted_bench(args)), flush=True)

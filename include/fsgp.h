@@ -378,6 +378,24 @@ int fsgp_step_noalloc(int32_t model, const fsgp_params *params, const int32_t *r
                       uint64_t rng_seed, const uint32_t *cur_planes, uint32_t *next_planes,
                       uint64_t *plane_counts, void *stream);
 
+/* Hegselmann-Krause opinion dynamics (Appendix A.2; Table 1's continuous HK row): R
+ * independent opinion vectors (realizations), updated synchronously for T steps.  At
+ * each step node i takes the mean of the opinions h_j of its in-neighbours j (Sec. 2's
+ * N^-(i); arcs with multiplicity; i itself only through a self-loop) with
+ * |h_i - h_j| < eps (strict, as in the appendix's message definition); with no such
+ * neighbour it keeps its opinion (the appendix's NaN case).  Single precision: eps is
+ * rounded to float, the sum is taken in col_idx order and divided once, so results are
+ * exactly those of that sequential loop.  No randomness.
+ *   h0: [R][n] float32 start opinions (finite), h_out: [R][n] float32 opinions after T
+ *     steps, changes: optional [T+1] u64, (node, realization) pairs whose opinion
+ *     changed at step k (changes[0] = 0); all three host or all device (flags).
+ * Uses the graph's workspace (4 * n * ceil(R/32) * 32 bytes, twice): the graph must not
+ * be used by another call meanwhile.  Host buffers: synchronises `stream`.
+ * Errors: EINVAL (eps negative or not finite, an opinion not finite, R outside
+ * [1, 4096], T < 0), ENOMEM, ECUDA. */
+int fsgp_hk(const fsgp_graph *g, const float *h0, int32_t R, int32_t T, double eps, float *h_out,
+            uint64_t *changes, uint32_t flags, void *stream);
+
 /* Self-test of the bounded grid barrier that separates the steps of the persistent step
  * loop (fsgp_options.persistent; a systems pattern, not in the paper).  Launches `ctas`
  * co-resident CTAs (cooperative launch) that pass the barrier `rounds` times; the barrier

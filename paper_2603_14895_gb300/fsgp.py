@@ -148,6 +148,9 @@ def load():
         lib.fsgp_surrogate_screen.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_double, ctypes.c_double, P, P]
         lib.fsgp_surrogate_screen.restype = ctypes.c_int
+        lib.fsgp_hk.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, P, P,
+                                ctypes.c_uint32, P]
+        lib.fsgp_hk.restype = ctypes.c_int
         lib.fsgp_graph_set_arc_weights.argtypes = [P, P, ctypes.c_uint32, P]
         lib.fsgp_graph_set_arc_weights.restype = ctypes.c_int
         lib.fsgp_selftest_barrier.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, P]
@@ -250,6 +253,31 @@ def fsgp_step_noalloc(model, params: fsgp_params, row_ptr, col_idx, n, nnz, R, t
                                     n, nnz, R, t, ctypes.c_uint64(rng_seed), _ptr(cur_planes),
                                     _ptr(next_planes), _ptr(plane_counts),
                                     _stream_handle(stream)))
+
+
+def hk(graph: Graph, h0, T: int, eps: float, stream=None):
+    """Hegselmann-Krause opinion dynamics (fsgp_hk): h0 [R][n] float32 (numpy: host
+    buffers, numpy results; torch CUDA tensor: device results).  Returns (h_T [R][n],
+    changes [T+1] u64)."""
+    import torch
+    if isinstance(h0, np.ndarray):
+        h0 = np.ascontiguousarray(np.atleast_2d(h0), dtype=np.float32)
+        out = np.zeros_like(h0)
+        changes = np.zeros(T + 1, dtype=np.uint64)
+        flags = PTR_HOST
+    else:
+        assert h0.dtype == torch.float32 and h0.is_cuda
+        h0 = h0.contiguous()
+        if h0.dim() == 1:
+            h0 = h0[None]
+        out = torch.empty_like(h0)
+        changes = torch.zeros(T + 1, dtype=torch.int64, device=h0.device)
+        flags = PTR_DEVICE
+    R, n = h0.shape
+    assert n == graph.n
+    _check(load().fsgp_hk(graph.handle, _ptr(h0), R, T, float(eps), _ptr(out), _ptr(changes), flags,
+                          _stream_handle(stream)))
+    return out, changes
 
 
 def fsgp_graph_set_arc_weights(h, w, stream=None) -> None:
