@@ -5,8 +5,8 @@
 //
 // GB300 layout: opinions are [n][Rp] float32 (Rp = R rounded up to 32), so that the 32
 // lanes of a warp are 32 realizations of one node and every gathered in-neighbour is one
-// 128-byte row segment.  One warp per (node, 32-realization group), hub rows first (the
-// degree-bucket order); the arcs of a row are visited in col_idx order and summed in
+// 128-byte row segment.  One warp per node and up to two 32-realization groups, hub rows
+// first (the degree-bucket order); the arcs of a row are visited in col_idx order and summed in
 // single precision with one division, the order the definition's sum is taken in, so
 // that the result is exactly the sequential one.
 #include <cuda_runtime.h>
@@ -49,53 +49,72 @@ __global__ void k_hk_check(const float *__restrict__ h, int64_t m, int32_t *bad)
     }
 }
 
-constexpr int kHkUnroll = 8;   // gathered rows in flight per lane
+constexpr int kHkUnroll = 8;   // gathered rows in flight per lane and group
+constexpr int kHkMaxVG = 2;    // 32-realization groups of one node per warp
 
-// One synchronous step.  changes: (node, realization) pairs whose opinion changed.
+// One synchronous step.  A warp takes VG consecutive 32-realization groups of one node
+// (the column indices are loaded once for all of them, and VG x kHkUnroll gathered rows
+// are in flight per lane).  changes: (node, realization) pairs whose opinion changed.
+template <int VG>
 __global__ void __launch_bounds__(256) k_hk_step(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                                                  const int32_t *__restrict__ order, int32_t n, int32_t R, int32_t Rp,
                                                  float eps, const float *__restrict__ cur, float *__restrict__ nxt,
                                                  unsigned long long *changes) {
     const int lane = threadIdx.x & 31;
     const int G = Rp >> 5;
-    const int64_t items = (int64_t)n * G;
+    const int GW = (G + VG - 1) / VG;   // warp items per node
+    const int64_t items = (int64_t)n * GW;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long ch = 0ull;
     for (int64_t it = gwarp; it < items; it += nwarps) {
-        const int64_t q = it / G;
-        const int32_t gi = (int32_t)(it - q * G);
+        const int64_t q = it / GW;
+        const int32_t g0 = (int32_t)(it - q * GW) * VG;
         const int32_t i = __ldg(order + q);
-        const int32_t r = gi * 32 + lane;
-        const float *base = cur + r;
-        const float hi = base[(size_t)i * Rp];
+        const float *base = cur + g0 * 32 + lane;
+        float hi[VG], sum[VG];
+        int32_t cnt[VG];
+#pragma unroll
+        for (int v = 0; v < VG; ++v) {
+            hi[v] = g0 + v < G ? base[(size_t)i * Rp + v * 32] : 0.0f;
+            sum[v] = 0.0f;
+            cnt[v] = 0;
+        }
         const int32_t beg = __ldg(row_ptr + i), end = __ldg(row_ptr + i + 1);
-        float sum = 0.0f;
-        int32_t cnt = 0;
         for (int32_t e0 = beg; e0 < end; e0 += 32) {
             // 32 column indices at once, one per lane, handed out by shuffles
             const int32_t mine = e0 + lane < end ? __ldg(col + e0 + lane) : 0;
             const int m = min(32, end - e0);
             for (int a0 = 0; a0 < m; a0 += kHkUnroll) {
-                float hj[kHkUnroll];
+                float hj[kHkUnroll][VG];
 #pragma unroll
                 for (int u = 0; u < kHkUnroll; ++u) {
                     const int32_t j = __shfl_sync(0xffffffffu, mine, (a0 + u) & 31);
-                    hj[u] = a0 + u < m ? base[(size_t)j * Rp] : 0.0f;
+#pragma unroll
+                    for (int v = 0; v < VG; ++v)
+                        hj[u][v] = (a0 + u < m && g0 + v < G) ? base[(size_t)j * Rp + v * 32] : 0.0f;
                 }
 #pragma unroll
                 for (int u = 0; u < kHkUnroll; ++u) {
-                    if (a0 + u < m && fabsf(__fsub_rn(hi, hj[u])) < eps) {
-                        sum = __fadd_rn(sum, hj[u]);
-                        ++cnt;
+#pragma unroll
+                    for (int v = 0; v < VG; ++v) {
+                        if (a0 + u < m && fabsf(__fsub_rn(hi[v], hj[u][v])) < eps) {
+                            sum[v] = __fadd_rn(sum[v], hj[u][v]);
+                            ++cnt[v];
+                        }
                     }
                 }
             }
         }
-        const float out = cnt > 0 ? __fdiv_rn(sum, (float)cnt) : hi;
-        nxt[(size_t)i * Rp + r] = out;
-        const unsigned chm = __ballot_sync(0xffffffffu, r < R && out != hi);
-        if (lane == 0) ch += (unsigned long long)__popc(chm);
+#pragma unroll
+        for (int v = 0; v < VG; ++v) {
+            if (g0 + v >= G) break;   // uniform over the warp
+            const int32_t r = (g0 + v) * 32 + lane;
+            const float out = cnt[v] > 0 ? __fdiv_rn(sum[v], (float)cnt[v]) : hi[v];
+            nxt[(size_t)i * Rp + r] = out;
+            const unsigned chm = __ballot_sync(0xffffffffu, r < R && out != hi[v]);
+            if (lane == 0) ch += (unsigned long long)__popc(chm);
+        }
     }
     __shared__ unsigned long long s_ch;
     if (threadIdx.x == 0) s_ch = 0ull;
@@ -161,11 +180,18 @@ extern "C" int fsgp_hk(const fsgp_graph *gc, const float *h0, int32_t R, int32_t
     FSGP_CUDA(cudaMemsetAsync(d_ch, 0, sizeof(unsigned long long) * ((size_t)T + 1), s));
     if (n > 0) k_hk_in<<<grid_el, 256, 0, s>>>(src, n, R, Rp, buf0);
     const float eps_f = (float)eps;
-    const int64_t warps = (int64_t)n * (Rp / 32);
+    const int G = Rp / 32;
+    const int VG = std::min(G, kHkMaxVG) >= 4 ? 4 : (std::min(G, kHkMaxVG) >= 2 ? 2 : 1);
+    const int64_t warps = (int64_t)n * ((G + VG - 1) / VG);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, (int64_t)g->sm_count * 8));
     float *cur = buf0, *nxt = buf1;
     for (int32_t k = 1; k <= T && n > 0; ++k) {
-        k_hk_step<<<grid, 256, 0, s>>>(g->row_ptr, g->col, g->rows_sorted, n, R, Rp, eps_f, cur, nxt, d_ch + k);
+        if (VG == 4)
+            k_hk_step<4><<<grid, 256, 0, s>>>(g->row_ptr, g->col, g->rows_sorted, n, R, Rp, eps_f, cur, nxt, d_ch + k);
+        else if (VG == 2)
+            k_hk_step<2><<<grid, 256, 0, s>>>(g->row_ptr, g->col, g->rows_sorted, n, R, Rp, eps_f, cur, nxt, d_ch + k);
+        else
+            k_hk_step<1><<<grid, 256, 0, s>>>(g->row_ptr, g->col, g->rows_sorted, n, R, Rp, eps_f, cur, nxt, d_ch + k);
         std::swap(cur, nxt);
     }
     FSGP_CUDA(cudaGetLastError());
