@@ -226,9 +226,13 @@ constexpr int min_ctas() { return V == 4 ? 2 : (V == 2 ? (WIDE ? 3 : 4) : 4); }
 // step), 1 = mid rows, 3 = rows with 4..15 in-arcs (dense steps only).
 // CG: the state planes are read through L2 only (the persistent step loop, which reads
 // in one launch the planes that other CTAs wrote at the previous step).
-template <int MODEL, int V, int TEAM, bool WARP_ROW, int BT, bool CG>
+// AG (team rows only): each row is taken by AG teams that split its arcs (every AG-th
+// group of 4 arcs) and merge their counts by shuffles; the first team decides.  Shorter
+// per-thread chains for small graphs, whose steps are bound by the longest chain.
+template <int MODEL, int V, int TEAM, bool WARP_ROW, int BT, bool CG, int AG = 1>
 __device__ __forceinline__ void rows_body(const StepArgs &A, int which, int32_t *s_lane,
                                           unsigned long long *s_pc) {
+    static_assert(AG == 1 || (!WARP_ROW && TEAM * AG <= 32), "arc groups: team rows within a warp");
     constexpr int B = WARP_ROW ? kWideBits : BT;
     constexpr int TPW = 32 / TEAM;
     constexpr int SW = TEAM * V;
@@ -259,7 +263,8 @@ __device__ __forceinline__ void rows_body(const StepArgs &A, int which, int32_t 
     const int tl = lane % TEAM;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    constexpr int RPI = WARP_ROW ? 1 : TPW;
+    constexpr int RPI = WARP_ROW ? 1 : TPW / AG;
+    const int grp = team % AG;          // arc group of the row (AG > 1)
     const int list_slot = A.k & 1;
     const int64_t nitems = nrows * A.nslices;
     Accum acc;
@@ -273,7 +278,7 @@ __device__ __forceinline__ void rows_body(const StepArgs &A, int which, int32_t 
     for (int i = 0; i < V; ++i) d0[i] = d1[i] = d2[i] = 0;
 
     for (int64_t base = gwarp * RPI; base < nitems; base += nwarps * RPI) {
-        const int64_t item = WARP_ROW ? base : base + team;
+        const int64_t item = WARP_ROW ? base : base + team / AG;
         const bool has_row = item < nitems;
         const int64_t ridx = has_row ? item / A.nslices : 0;
         const int slice = has_row ? (int)(item - ridx * A.nslices) : 0;
@@ -332,7 +337,8 @@ __device__ __forceinline__ void rows_body(const StepArgs &A, int which, int32_t 
             if (WARP_ROW)
                 gather_arcs<MODEL, V, B, CG>(A, (int64_t)beg + 4 * team, end, 4 * TPW, arcb, w0, need, ic_thr, x, c, newly);
             else
-                gather_arcs<MODEL, V, B, CG>(A, beg, end, 4, arcb, w0, need, ic_thr, x, c, newly);
+                gather_arcs<MODEL, V, B, CG>(A, (int64_t)beg + 4 * grp, end, 4 * AG, arcb, w0, need, ic_thr, x, c,
+                                             newly);
         }
         constexpr bool SPLIT = WARP_ROW && TPW >= V;   // enough teams to give each word one
         if constexpr (SPLIT && V == 2 && ModelTraits<MODEL>::counts) {
@@ -355,10 +361,10 @@ __device__ __forceinline__ void rows_body(const StepArgs &A, int which, int32_t 
             }
 #pragma unroll
             for (int b = 0; b < B; ++b) c[1][b] = c[0][b];
-        } else if (WARP_ROW) {
+        } else if (WARP_ROW || AG > 1) {
             // merge the teams' partial results (the warp is converged here)
 #pragma unroll
-            for (int o = TEAM; o < 32; o <<= 1) {
+            for (int o = TEAM; o < (WARP_ROW ? 32 : TEAM * AG); o <<= 1) {
 #pragma unroll
                 for (int i = 0; i < V; ++i) {
                     if constexpr (ModelTraits<MODEL>::counts) {
@@ -419,7 +425,7 @@ __device__ __forceinline__ void rows_body(const StepArgs &A, int which, int32_t 
             for (int o = 1; o < 32; o <<= 1) fl |= __shfl_xor_sync(0xffffffffu, fl, o);
             writer = has_row && team == 0;
         } else {
-        writer = has_row && (!WARP_ROW || team == 0);
+        writer = has_row && (WARP_ROW ? team == 0 : grp == 0);
         if (writer) {
             // own state again (L1/L2-resident): not kept live across the gather
             uint32_t s0[V], s1[V], s2[V];
@@ -491,7 +497,7 @@ __global__ void __launch_bounds__(kBlock, min_ctas<V, WARP_ROW>()) k_rows(StepAr
 // (CG loads): a CTA reads at step k the words other CTAs wrote at step k-1.
 // (bounded for 2 resident CTAs per SM: the loop is meant for graphs that fill a few CTAs
 // per SM at most, and the body then keeps its state in registers)
-template <int MODEL, int V, int TEAM, bool WARP_ROW, int BT = kSmallBits>
+template <int MODEL, int V, int TEAM, bool WARP_ROW, int BT = kSmallBits, int AG = 1>
 __global__ void __launch_bounds__(kBlock, 2)
     k_rows_persist(const __grid_constant__ StepArgs A0, const __grid_constant__ PersistArgs Q) {
     extern __shared__ int32_t s_lane[];
@@ -529,7 +535,7 @@ __global__ void __launch_bounds__(kBlock, 2)
             if (blockIdx.x == 0 && threadIdx.x == 0) C->stop = 1;
             break;
         }
-        rows_body<MODEL, V, TEAM, WARP_ROW, BT, true>(sA, WARP_ROW ? 1 : 0, s_lane, s_pc);
+        rows_body<MODEL, V, TEAM, WARP_ROW, BT, true, AG>(sA, WARP_ROW ? 1 : 0, s_lane, s_pc);
         if (!grid_barrier(&C->bar_count, &C->bar_gen, gridDim.x, &C->err, Q.spin_limit)) break;
         if (blockIdx.x == 0 && threadIdx.x == 0) C->steps_done = k;
         if (cascade)
@@ -1155,12 +1161,15 @@ int occupancy_rows(int V, int TEAM, size_t smem, RowOccupancy *o) {
 template <int MODEL, int TEAM>
 int launch_persist_t(const StepArgs &A, const PersistArgs &Q, int grid, size_t smem, int sm_count,
                      cudaStream_t s, int *grid_out) {
-    auto kern = k_rows_persist<MODEL, 1, TEAM, false, kSmallBits>;
+    // up to 4 teams per row split its arcs (within a warp)
+    constexpr int AG = TEAM >= 32 ? 1 : (TEAM >= 16 ? 2 : 4);
+    auto kern = k_rows_persist<MODEL, 1, TEAM, false, kSmallBits, AG>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor (persistent)");
     if (per_sm < 1) return FSGP_EUNSUPPORTED;
-    grid = std::max(1, std::min(grid, per_sm * sm_count));
+    // one work item (row slice) per team of AG teams: AG times the launched loop's CTAs
+    grid = std::max(1, std::min(grid * AG, per_sm * sm_count));
     StepArgs a = A;
     PersistArgs q = Q;
     void *args[] = {&a, &q};
