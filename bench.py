@@ -1013,8 +1013,11 @@ def main():
         rp = torch.from_numpy(g.row_ptr).pin_memory()
         ci = torch.from_numpy(g.col_idx).pin_memory()
         sd = torch.from_numpy(seeds.astype(np.int32)).pin_memory()
-        host_out = {m: {"counts": np.zeros((1, T + 1, 3), np.uint64),
-                        "freq": np.zeros((1, 3, g.n), np.uint32)} for m in MODELS}
+        # result buffers in pinned host memory (what a caller streaming results would use)
+        def pinned(shape, dt_torch):
+            return torch.zeros(shape, dtype=dt_torch).pin_memory().numpy()
+        host_out = {m: {"counts": pinned((1, T + 1, 3), torch.int64).view(np.uint64),
+                        "freq": pinned((1, 3, g.n), torch.int32).view(np.uint32)} for m in MODELS}
         n_e2e = max(1, args.steps)
         graph.close()
         torch.cuda.synchronize()
