@@ -33,6 +33,18 @@ def test_hk_matches_oracle(cuda_lib, gi, R, eps):
     assert np.array_equal(ch.astype(np.uint64), och)
 
 
+def test_hk_max_realizations(cuda_lib):
+    """R = 4096 (128 realization groups, two per warp) on a small graph."""
+    f = cuda_lib
+    g = W.ba(300, 3, seed=941)
+    graph = f.Graph(g.row_ptr, g.col_idx)
+    h0 = _h0(4096, g.n, 942)
+    h, ch = f.hk(graph, h0, 10, 0.3)
+    oh, och = O.hk(g.row_ptr, g.col_idx, h0, T=10, eps=0.3)
+    assert np.array_equal(h.view(np.uint32), oh.view(np.uint32))
+    assert np.array_equal(ch.astype(np.uint64), och)
+
+
 def test_hk_device_buffers_and_t0(cuda_lib):
     import torch
     f = cuda_lib
