@@ -157,6 +157,26 @@ def _mc_targets(f, graph, seeds, beta, R=256, T=50, rng_seed=5):
     return (fr[1] + fr[2]) / R, out
 
 
+def test_screening_equals_full_forward(cuda_lib):
+    """Every candidate's screening score equals the sum of a full forward's
+    probabilities, for hub seeds, repeated seeds, a single repeated node and candidates
+    screened one after another (the seed features are restored between candidates)."""
+    f = cuda_lib
+    g, graph = _setup(f, n=4000, m=4, seed=421)
+    sg = f.Surrogate(15)
+    hubs = np.argsort(-g.in_degree())[:20].astype(np.int32)
+    rng = np.random.default_rng(422)
+    cands = [np.array([hubs[0]] * 6, np.int32), hubs[:6].copy()]
+    cands += [rng.choice(g.n, 6).astype(np.int32) for _ in range(10)]
+    cands += [np.array([hubs[1], 7, 7, 8, 9, 10], np.int32), np.array([g.n - 1] * 6, np.int32)]
+    cands = np.stack(cands)
+    scores = sg.screen(graph, cands, 0.02, 0.1)
+    for c in range(len(cands)):
+        p = sg.forward(graph, cands[c], 0.02, 0.1)
+        want = float(p.sum())
+        assert abs(want - scores[c]) <= 1e-3 * max(1.0, abs(want)), (c, want, scores[c])
+
+
 def _mixed_set(rng, n, hubs, n_hub, k=5):
     """k seeds of which n_hub come from the highest-degree nodes: seed sets whose Monte
     Carlo spread genuinely differs, so a ranking has something to find."""
