@@ -10,8 +10,9 @@ partitions, every node contributed by exactly one of them).  The load of every
 partition is within w_max of W / d.
 
 Host logic only (numpy).  One GB300 holds graphs of a billion arcs (an R-MAT scale-26
-graph with its tables takes 10.7 GB of 288), so the propagation kernels run
-unpartitioned; this module is the partitioner and its subgraph extraction.
+graph with its tables takes 14.7 GB of 288), so the propagation kernels normally run
+unpartitioned; this module is the partitioner and its subgraph extraction, and
+partitioned.py runs the step partition by partition.
 """
 from __future__ import annotations
 
