@@ -291,7 +291,9 @@ typedef struct {
  * spread over n_streams streams (longest first onto the least loaded), each issued by
  * its own host thread.  Work is ordered after prior work on `stream`, and `stream`
  * waits for all of it; the call returns once everything is enqueued.  A graph may
- * appear in several requests but must not be used by other calls meanwhile.
+ * appear in several requests but must not be used by other calls meanwhile.  Small
+ * graphs run the launched step loop, never the persistent one (the streams share the
+ * GPU's SMs, which a cooperative grid would have to wait for).
  * Errors: EINVAL (any bad request: nothing is run), ENOMEM, ECUDA. */
 int fsgp_batch_run(const fsgp_request *reqs, int32_t n, const fsgp_batch_options *opt,
                    void *stream);

@@ -197,6 +197,9 @@ extern "C" int fsgp_batch_run(const fsgp_request *reqs, int32_t n, const fsgp_ba
             o = gm->tuned_opt;
         }
         o.capture_graph = bo.capture_graph >= 0 ? 1 : 0;
+        // the graphs share the GPU through concurrent streams: no persistent step loop,
+        // whose grid barrier would wait for CTAs that SMs busy with other streams hold
+        o.persistent = -1;
         tuned[g] = o;
     }
     // graphs to streams, longest first onto the least loaded stream
