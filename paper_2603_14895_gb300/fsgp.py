@@ -266,7 +266,8 @@ def hk(graph: Graph, h0, T: int, eps: float, stream=None):
         changes = np.zeros(T + 1, dtype=np.uint64)
         flags = PTR_HOST
     else:
-        assert h0.dtype == torch.float32 and h0.is_cuda
+        if h0.dtype != torch.float32 or not h0.is_cuda:
+            raise TypeError("h0 must be a float32 numpy array or a float32 CUDA tensor")
         h0 = h0.contiguous()
         if h0.dim() == 1:
             h0 = h0[None]
@@ -274,7 +275,8 @@ def hk(graph: Graph, h0, T: int, eps: float, stream=None):
         changes = torch.zeros(T + 1, dtype=torch.int64, device=h0.device)
         flags = PTR_DEVICE
     R, n = h0.shape
-    assert n == graph.n
+    if n != graph.n:
+        raise ValueError(f"h0 has {n} columns, the graph {graph.n} nodes")
     _check(load().fsgp_hk(graph.handle, _ptr(h0), R, T, float(eps), _ptr(out), _ptr(changes), flags,
                           _stream_handle(stream)))
     return out, changes
@@ -289,7 +291,8 @@ def fsgp_graph_set_arc_weights(h, w, stream=None) -> None:
         flags = PTR_HOST
     else:
         import torch
-        assert w.dtype == torch.float32
+        if w.dtype != torch.float32:
+            raise TypeError("arc weights must be float32")
         w = w.contiguous()
         flags = PTR_DEVICE if w.is_cuda else PTR_HOST
     _check(load().fsgp_graph_set_arc_weights(h, _ptr(w), flags, _stream_handle(stream)))
@@ -328,7 +331,8 @@ class Graph:
             col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
             flags = PTR_HOST
         else:
-            assert row_ptr.dtype == torch.int32 and col_idx.dtype == torch.int32
+            if row_ptr.dtype != torch.int32 or col_idx.dtype != torch.int32:
+                raise TypeError("row_ptr and col_idx must be int32")
             row_ptr = row_ptr.contiguous()
             col_idx = col_idx.contiguous()
             flags = PTR_DEVICE if row_ptr.is_cuda else PTR_HOST
@@ -516,7 +520,8 @@ class Surrogate:
 
     def set_params(self, theta) -> None:
         t = np.ascontiguousarray(theta, dtype=np.float32)
-        assert t.size == self.n_params
+        if t.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {t.size}")
         _check(load().fsgp_surrogate_params(self.handle, None, t.ctypes.data))
 
     def forward(self, graph, seeds, beta, gamma, stream=None):

@@ -89,3 +89,22 @@ def test_binding_structs_match_the_header_layout(tmp_path):
     subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).decode().split()]
     assert got == expect
+
+
+def test_binding_rejects_bad_arguments_before_any_call():
+    """Argument errors in the binding raise TypeError/ValueError (not assertions, which
+    `python -O` strips) before the library is called."""
+    import types
+
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    from paper_2603_14895_gb300 import fsgp
+    g = types.SimpleNamespace(n=5, handle=None)
+    with pytest.raises(ValueError):
+        fsgp.hk(g, np.zeros((2, 4), np.float32), 3, 0.1)
+    with pytest.raises(TypeError):
+        fsgp.hk(g, torch.zeros((2, 5), dtype=torch.float64), 3, 0.1)
+    with pytest.raises(TypeError):
+        fsgp.fsgp_graph_set_arc_weights(None, torch.zeros(4, dtype=torch.float64))
+    with pytest.raises(TypeError):
+        fsgp.Graph(torch.zeros(3, dtype=torch.int64), torch.zeros(2, dtype=torch.int32))
