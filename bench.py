@@ -217,14 +217,20 @@ def workload_config(g, seeds):
             "l2": "inputs larger than L2 (4.3 GB arcs, 8.6 GB state planes); no flush"}
 
 
-def cpu_baseline(g, seeds):
+def cpu_baseline(g, seeds, min_seconds=10.0):
+    """The oracle's first SIR step on the full graph, in blocks of one realization per
+    core: at least one block, then more until min_seconds of CPU work or all R
+    realizations are done."""
     import oracle as O
     cores = os.cpu_count() or 1
-    n_real, T_s = cores, 1
-    t = time.perf_counter()
-    O.simulate(O.SIR, g.row_ptr, g.col_idx, seeds, beta=BETA, gamma=GAMMA, R=R, T=T_s,
-               rng_seed=RNG_SEED, r_lo=0, n_real=n_real, nthreads=cores, outputs=("counts",))
-    sec = time.perf_counter() - t
+    T_s, n_real, sec = 1, 0, 0.0
+    while n_real == 0 or (sec < min_seconds and n_real < R):
+        blk = min(cores, R - n_real)
+        t = time.perf_counter()
+        O.simulate(O.SIR, g.row_ptr, g.col_idx, seeds, beta=BETA, gamma=GAMMA, R=R, T=T_s,
+                   rng_seed=RNG_SEED, r_lo=n_real, n_real=blk, nthreads=cores, outputs=("counts",))
+        sec += time.perf_counter() - t
+        n_real += blk
     return {"value": float(g.nnz) * n_real * T_s / sec, "unit": "edge-realization-steps/s",
             "cores": cores, "kind": "oracle",
             "sample": f"SIR, {n_real} realizations x {T_s} steps on the full graph, "

@@ -27,3 +27,23 @@ def test_reference_arm_json_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
+
+
+def test_cpu_baseline_blocks_and_rate():
+    """bench.cpu_baseline times the oracle in blocks of one realization per core: with no
+    time floor it runs one block, with a floor it stops at R at the latest, and its rate
+    is arcs x realizations x steps over the seconds it reports."""
+    import re
+    import sys
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import bench
+    import workloads as W
+    g = W.rmat(12, 8, seed=11)
+    s = W.seed_set(g.n, 20, seed=12)
+    cores = os.cpu_count() or 1
+    one = bench.cpu_baseline(g, s, min_seconds=0.0)
+    m = re.match(r"SIR, (\d+) realizations x 1 steps on the full graph, ([0-9.]+) s", one["sample"])
+    assert m and int(m.group(1)) == min(cores, bench.R)
+    assert one["cores"] == cores and one["kind"] == "oracle" and one["value"] > 0
+    full = bench.cpu_baseline(g, s, min_seconds=1e9)
+    assert full["sample"].startswith(f"SIR, {bench.R} realizations")
